@@ -1,0 +1,383 @@
+"""AIDW benchmark: pair-evaluations per second of the FP32-compensated path on GB300.
+
+Workload (one step): AIDW of 1,048,576 query points against 1,048,576 data points, uniform in
+[0,1000]^2 (A = 1e6), z = sin(x/100) + cos(y/150) + 0.05 N(0,1), k = 10, levels (1,2,3,4,5),
+R_min = 0, R_max = 2 -- the paper's largest size class (Sec. 4: as many queries as data points,
+uniform in a square), seeded synthetic data. A pair-evaluation is one (query, data point) pair
+carried through both phases (kNN scan and weighted sum); a step is n * m of them.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0). Under torchrun every rank runs its own full-size problem (query
+sets are independent; no collective on the data path) and the value is all ranks' pairs over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AIDW pair-evals/s (FP32-compensated path)"
+UNIT = "pair-evals/s"
+N_DATA = 1 << 20
+M_QUERY = 1 << 20
+L2_FLUSH_BYTES = 256 << 20
+# Algorithmic work per pair-evaluation (minimum the method needs): phase 1: 2 sub, 1 mul,
+# 1 fma, 1 compare; phase 2: 2 sub, 1 mul, 1 fma, 1 fma (power scale), 1 add, 1 fma; plus one
+# MUFU lg2 and one MUFU ex2.
+FP32_OPS_P1, FP32_OPS_P2, MUFU_OPS_P2 = 5, 7, 2
+LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
+
+
+def workload_config(wl):
+    return {"workload": "uniform_paper_1M_x_1M", "n_data": wl.n, "m_query": wl.m, "k": wl.k,
+            "levels": list(wl.levels), "r_min": wl.r_min, "r_max": wl.r_max, "area": wl.area,
+            "domain": "[0,1000]^2", "seed": 0,
+            "l2": "flushed between timed steps by a 256 MiB write (outside the timed events)"}
+
+
+# ---- clocks ------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- distributed plumbing -------------------------------------------------------------------
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU baseline (the FP64 oracle, as it stands) --------------------------------------------
+
+def oracle_rate(wl, target_s: float, threads: int):
+    """Times the oracle on a seeded query sample sized for about target_s seconds of CPU work;
+    returns (pair-evals/s, sample description, threads)."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(123)
+    q = 64
+    idx = rng.choice(wl.m, q, replace=False)
+    t0 = time.perf_counter()
+    oracle.interpolate(wl.x, wl.y, wl.z, wl.area, wl.qx[idx], wl.qy[idx], wl.k, wl.levels,
+                       threads=threads)
+    dt = time.perf_counter() - t0
+    q2 = int(min(wl.m, max(q, q * target_s / max(dt, 1e-3))))
+    q2 = max(threads, (q2 // threads) * threads)
+    idx = rng.choice(wl.m, q2, replace=False)
+    t0 = time.perf_counter()
+    oracle.interpolate(wl.x, wl.y, wl.z, wl.area, wl.qx[idx], wl.qy[idx], wl.k, wl.levels,
+                       threads=threads)
+    dt = time.perf_counter() - t0
+    return (q2 * wl.n) / dt, f"{q2} seeded queries x all {wl.n} data points, {dt:.1f} s", threads
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    from paper_1511_02186_gb300 import workloads
+    wl = workloads.uniform_paper(0)
+    threads = os.cpu_count() or 1
+    vals = []
+    for _ in range(args.warmup):
+        oracle_rate_small(wl, threads)
+    for _ in range(args.steps):
+        vals.append(oracle_rate_small(wl, threads))
+    v = statistics.median([x[0] for x in vals])
+    sample = vals[0][1]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median([x[2] for x in vals]) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_rate_small(wl, threads):
+    import oracle
+    rng = np.random.default_rng(len(wl.qx))
+    q = 8 * threads
+    idx = rng.choice(wl.m, q, replace=False)
+    t0 = time.perf_counter()
+    oracle.interpolate(wl.x, wl.y, wl.z, wl.area, wl.qx[idx], wl.qy[idx], wl.k, wl.levels,
+                       threads=threads)
+    dt = time.perf_counter() - t0
+    return q * wl.n / dt, f"{q} seeded queries x all {wl.n} data points per step", dt
+
+
+# ---- GPU arm -----------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_1511_02186_gb300 import aidw, workloads
+    import __graft_entry__
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    wl = workloads.uniform_paper(0)
+    ctx = aidw.Context(local)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)
+    qy = torch.as_tensor(wl.qy, dtype=torch.float32, device=dev)
+    out = torch.empty(wl.m, dtype=torch.float32, device=dev)
+    p = aidw.default_params(k=wl.k, levels=wl.levels)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.interpolate(ds, qx, qy, p, out=out, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ctx.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ktimes = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        kt = ctx.kernel_times()  # waits for this step's events
+        ktimes.append(kt)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ctx.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(total_s, world, dev)
+    pairs = float(wl.n) * wl.m
+    value = world * pairs * args.steps / total_s
+
+    # Roofline of the dominant kernel (largest device time per step).
+    kn = statistics.mean(t.knn_ms for t in ktimes)
+    kw = statistics.mean(t.weights_ms for t in ktimes)
+    ks = statistics.mean(t.select_ms for t in ktimes)
+    kf = statistics.mean(t.finalize_ms for t in ktimes)
+    rates = ctx.pipe_rates()
+    sm = rates.sm_count
+    sm_mhz_peak = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_mhz_peak = float(json.load(f).get("sm_max_mhz", sm_mhz_peak))
+    except (OSError, ValueError):
+        pass
+    clk_hz = sm_mhz_peak * 1e6
+
+    def peak_pairs(fp32_ops, mufu_ops):
+        # mufu_ops is one lg2 plus one ex2 per pair when nonzero.
+        mufu_clk = (1.0 / rates.ex2_per_clk_sm + 1.0 / rates.lg2_per_clk_sm) if mufu_ops else 0.0
+        per_pair_clk = max(fp32_ops / LANES_PER_SM, mufu_clk,
+                           (fp32_ops + mufu_ops) / LANES_PER_SM)
+        return sm * clk_hz / per_pair_clk
+
+    dominant = "weights" if kw >= kn else "knn"
+    if dominant == "weights":
+        achieved = pairs / (kw / 1e3)
+        peak = peak_pairs(FP32_OPS_P2, MUFU_OPS_P2)
+    else:
+        achieved = pairs / (kn / 1e3)
+        peak = peak_pairs(FP32_OPS_P1, 0)
+    step_peak = peak_pairs(FP32_OPS_P1 + FP32_OPS_P2, MUFU_OPS_P2)
+    kernel_sum_s = (kn + kw + ks + kf) / 1e3
+
+    # FP64 path on a query sample of the same dataset (same per-query work).
+    q64 = 8192
+    idx = torch.as_tensor(np.random.default_rng(9).choice(wl.m, q64, replace=False))
+    qx64 = torch.as_tensor(wl.qx, dtype=torch.float64, device=dev)[idx.to(dev)].contiguous()
+    qy64 = torch.as_tensor(wl.qy, dtype=torch.float64, device=dev)[idx.to(dev)].contiguous()
+    p64 = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64)
+    ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = q64 * wl.n / (e0.elapsed_time(e1) / 1e3)
+
+    # End to end through the public API with host buffers: dataset upload (FP64 host arrays),
+    # query upload from pinned memory, interpolation, result download.
+    hqx = torch.as_tensor(wl.qx, dtype=torch.float32).pin_memory()
+    hqy = torch.as_tensor(wl.qy, dtype=torch.float32).pin_memory()
+    hout = torch.empty(wl.m, dtype=torch.float32).pin_memory()
+    hx, hy, hz = (torch.as_tensor(a, dtype=torch.float64).pin_memory() for a in
+                  (wl.x, wl.y, wl.z))
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d2 = ctx.create_dataset(hx, hy, hz, wl.area)
+        ctx.interpolate(d2, hqx, hqy, p, out=hout, stream=stream.cuda_stream)
+        d2.destroy()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_val = world * pairs * e2e_steps / e2e_s
+    h2d = 3 * 8 * wl.n + 2 * 4 * wl.m
+    d2h = 4 * wl.m
+
+    line = None
+    if rank == 0:
+        threads = os.cpu_count() or 1
+        cpu_v, cpu_sample, cpu_threads = oracle_rate(wl, args.cpu_seconds, threads)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded uniform points, BASELINE config 2 shape)",
+            "config": workload_config(wl),
+            "queries_per_s": world * wl.m * args.steps / total_s,
+            "kernel_ms": {"knn": kn, "select": ks, "weights": kw, "finalize": kf},
+            "plan": {"knn_splits": ktimes[0].splits, "w_splits": ktimes[0].weight_splits,
+                     "query_blocks": ktimes[0].query_blocks},
+            "roofline": {"bound": "alu", "kernel": f"f32_{dominant}_kernel",
+                         "achieved": achieved, "peak": peak, "unit": UNIT,
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": (f"{sm} SMs x {sm_mhz_peak:.0f} MHz (max SM clock) / "
+                                        "max(FP32 ops / 128 lanes, 1/ex2 + 1/lg2 measured MUFU "
+                                        "rates per clk per SM, all ops / 128 issue slots)"),
+                         "step_achieved": pairs / kernel_sum_s, "step_peak": step_peak,
+                         "step_frac": (pairs / kernel_sum_s) / step_peak},
+            "pipe_rates": {"ffma_per_clk_sm": rates.ffma_per_clk_sm,
+                           "ex2_per_clk_sm": rates.ex2_per_clk_sm,
+                           "lg2_per_clk_sm": rates.lg2_per_clk_sm,
+                           "fmnmx_per_clk_sm": rates.fmnmx_per_clk_sm,
+                           "probe_sm_mhz": rates.sm_clock_mhz},
+            "fp64_path": {"value": fp64_rate, "unit": UNIT,
+                          "sample": f"{q64} seeded queries x all {wl.n} data points"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "includes": "dataset upload + conversion, query upload, both phases, "
+                                "result download"},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads,
+                             "kind": "oracle", "sample": cpu_sample},
+            "paper_context": {"gt730m_tiled_soa_1000K_pair_evals_s": 6.2e9,
+                              "note": "GeForce GT 730M, FP32, N = 1,024,000, transfers "
+                                      "included; different hardware and workload"},
+        }
+    ds.destroy()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

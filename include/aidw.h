@@ -1,0 +1,215 @@
+/*
+ * aidw.h -- C ABI of the GB300 (sm_103a) Adaptive Inverse Distance Weighting library.
+ *
+ * The method is AIDW as defined by Mei, Xu & Xu, "Accelerating Adaptive IDW Interpolation
+ * Algorithm on a Single GPU" (arXiv 1511.02186):
+ *   phase 1 (Sec. 2.2, Steps 1-3; kNN per Sec. 3.1.2): for every query point find its k nearest
+ *           data points, form r_obs (Eq. 3) against r_exp (Eq. 2), the statistic R (Eq. 4), the
+ *           fuzzy membership mu_R (Eq. 5) and the adaptive power alpha (Eq. 6);
+ *   phase 2 (Sec. 2.1, Eq. 1; Sec. 3.2.1): Z = sum_i z_i d_i^-alpha / sum_i d_i^-alpha over ALL
+ *           n data points.
+ *
+ * Conventions for every entry point:
+ *   - Return value: AIDW_OK (0) or a negative AIDW_ERR_* status; no entry point throws, aborts
+ *     or prints. aidw_status_string() names a status.
+ *   - Notation: n data points, m query points, k neighbours, A the study area.
+ *   - Pointers to caller arrays may be host memory (pageable or pinned) or device memory of the
+ *     context's device; the library tells them apart with cudaPointerGetAttributes. A call that
+ *     touches any host array copies through library-owned device buffers and returns only once
+ *     its results are in the caller's host arrays. A call whose arrays are all on the device is
+ *     stream-ordered: it returns after enqueuing its kernels on the given stream.
+ *   - Caller arrays remain caller-owned; the library never frees them and keeps no reference to
+ *     them after the call returns (asynchronous calls: after the stream reaches the work).
+ *   - Datasets are copied into library-owned device memory at creation and stay resident until
+ *     destroyed.
+ *   - A context is not thread-safe: serialise calls on one context, or use one per thread.
+ */
+#ifndef AIDW_H
+#define AIDW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------- */
+#define AIDW_OK 0
+#define AIDW_PENDING 1             /* request admitted, results not ready yet */
+#define AIDW_ERR_INVALID_ARG (-1)  /* a size, parameter or input value is outside the domain */
+#define AIDW_ERR_OOM (-2)          /* device memory or the context's HBM budget is exhausted */
+#define AIDW_ERR_AGAIN (-3)        /* serving queue full: resubmit later */
+#define AIDW_ERR_TIMEOUT (-4)      /* a bounded wait ran out (host wait or an on-device wait) */
+#define AIDW_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define AIDW_ERR_NOT_FOUND (-6)    /* unknown dataset or request handle */
+#define AIDW_ERR_UNSUPPORTED (-7)  /* device is not sm_103 or an option is not built */
+
+/* ---- precisions and dtypes ------------------------------------------------------------ */
+/* AIDW_F32C: distances, kNN selection and weights in FP32; the two weighted sums in FP32 with
+ * Kahan-compensated merges; alpha mapping (Eq. 2, 4, 5, 6) and the final ratio in FP64.
+ * Queries and the output are float arrays.
+ * AIDW_F64: every step in FP64; queries and the output are double arrays. */
+#define AIDW_F32C 0
+#define AIDW_F64 1
+
+#define AIDW_DTYPE_F32 0
+#define AIDW_DTYPE_F64 1
+
+/* Largest k supported by the kernels (the register-resident neighbour list holds 32). */
+#define AIDW_MAX_K 32
+
+typedef struct aidw_ctx aidw_ctx;
+typedef int64_t aidw_dataset;
+typedef int64_t aidw_request;
+
+/* Parameters of one interpolation (Sec. 2.2). */
+typedef struct aidw_params {
+    int32_t k;         /* neighbours for r_obs (Eq. 3); 1 <= k <= min(n, AIDW_MAX_K) */
+    int32_t precision; /* AIDW_F32C or AIDW_F64 */
+    double alpha[5];   /* the five levels alpha_1..alpha_5 of Eq. 6; finite, > 0 */
+    double r_min;      /* R_min of Eq. 5 (the paper suggests 0.0) */
+    double r_max;      /* R_max of Eq. 5 (the paper suggests 2.0); r_max > r_min, r_max > 0 */
+    uint32_t flags;    /* reserved, must be 0 */
+    int32_t reserved;  /* reserved, must be 0 */
+} aidw_params;
+
+/* Fills k = 10, precision = AIDW_F32C, alpha = {1,2,3,4,5}, r_min = 0, r_max = 2. The level
+ * values are not given by the paper (Eq. 6 leaves them to the user); these are a default. */
+void aidw_params_default(aidw_params *p);
+
+/* ---- context -------------------------------------------------------------------------- */
+/* Creates a context on CUDA device `device`. hbm_budget_bytes caps the device memory the
+ * context holds at once (datasets + per-call scratch); 0 means "whatever the device has".
+ * Returns AIDW_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
+int aidw_init(aidw_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Waits for the context's work, frees every dataset and buffer it owns, and the context. */
+int aidw_shutdown(aidw_ctx *ctx);
+
+/* ---- datasets (Sec. 3.2.1: the data points' coordinates and values) ------------------- */
+/* Copies n data points (x[i], y[i]) with values z[i] into library-owned device memory, as
+ * FP32 and FP64 structure-of-arrays copies padded to a tile multiple. `area` is the study
+ * area A of Eq. 2 (the paper does not say how A is obtained, so the caller supplies it).
+ * dtype is AIDW_DTYPE_F32 or AIDW_DTYPE_F64 for all three arrays.
+ * Errors: INVALID_ARG if n < 1, n > 2^31 - 2048, area is not finite and > 0, or any x, y, z
+ * is NaN or infinite (checked on the device after the copy); OOM if the memory or the budget
+ * runs out. This call is synchronous. */
+int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void *z, int64_t n,
+                        double area, int32_t dtype, aidw_dataset *out);
+
+/* Frees a dataset. Work already enqueued on it must have finished (the call synchronizes the
+ * device before freeing). */
+int aidw_destroy_dataset(aidw_ctx *ctx, aidw_dataset ds);
+
+/* Number of points and device bytes held by a dataset. */
+int aidw_dataset_info(aidw_ctx *ctx, aidw_dataset ds, int64_t *n, size_t *device_bytes);
+
+/* ---- interpolation -------------------------------------------------------------------- */
+/* AIDW at m query points (qx[j], qy[j]) against dataset ds.
+ *   qx, qy   m coordinates, float for AIDW_F32C, double for AIDW_F64
+ *   out      m predictions Z (Eq. 1), float for AIDW_F32C, double for AIDW_F64
+ *   out_alpha  nullable; m adaptive powers alpha (Eq. 6) as float
+ *   out_knn  nullable; m*k int32 data-point indices, row j holding query j's neighbours in
+ *            ascending distance, ties to the lower index (Sec. 3.1.2 with strict "<")
+ *   stream   cudaStream_t to order the work on (NULL: the legacy default stream)
+ * A query that coincides exactly with data points returns the mean z of those points (the
+ * limit of Eq. 1). m == 0 is a no-op. Errors: INVALID_ARG for a bad k, level, bound, size or
+ * (for host arrays) a non-finite query coordinate; on device arrays a non-finite query gives a
+ * NaN prediction instead. NOT_FOUND for an unknown dataset; OOM when scratch does not fit. */
+int aidw_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
+                     const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
+                     void *stream);
+
+/* Standard IDW (Sec. 2.1, Eq. 1) with one constant power `alpha` for all queries: phase 2 of
+ * AIDW alone. Same array conventions as aidw_interpolate; `precision` selects the path. */
+int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
+             double alpha, int32_t precision, void *out, void *stream);
+
+/* ---- batched launch (many datasets in one persistent kernel) -------------------------- */
+/* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays) and params.
+ * All entries of one batch share the precision AIDW_F32C. */
+typedef struct aidw_batch_item {
+    aidw_dataset ds;
+    const float *qx, *qy;
+    int64_t m;
+    aidw_params params;
+    float *out;
+    float *out_alpha; /* nullable */
+} aidw_batch_item;
+
+/* Runs every item through the persistent work-queue kernels on `stream` (stream-ordered).
+ * Each item's results equal those of aidw_interpolate on the same inputs within the FP32
+ * tolerance, whatever else is in the batch. */
+int aidw_interpolate_batch(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count,
+                           void *stream);
+
+/* ---- serving: asynchronous requests with continuous batching --------------------------- */
+/* Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host
+ * or device and must stay valid until aidw_poll/aidw_wait report completion). Requests are
+ * admitted by HBM footprint and batched into persistent launches by the context's serving
+ * thread, started on first use. Returns AIDW_ERR_AGAIN if the queue is full. */
+int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
+                const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
+                aidw_request *out_id);
+
+/* *done = 1 when the request has finished (its status is returned), else 0 and AIDW_PENDING. */
+int aidw_poll(aidw_ctx *ctx, aidw_request id, int32_t *done);
+
+/* Waits up to timeout_us microseconds (< 0: no limit) for a request; returns its status, or
+ * AIDW_ERR_TIMEOUT. */
+int aidw_wait(aidw_ctx *ctx, aidw_request id, int64_t timeout_us);
+
+/* Submit -> completion latency of a finished request in microseconds. */
+int aidw_request_latency_us(aidw_ctx *ctx, aidw_request id, double *latency_us);
+
+/* Forgets a finished request (its handle becomes unknown); AIDW_PENDING if not finished. */
+int aidw_release_request(aidw_ctx *ctx, aidw_request id);
+
+/* ---- diagnostics ---------------------------------------------------------------------- */
+const char *aidw_status_string(int status);
+
+/* Checks the context's on-device error word (set by a bounded wait inside a kernel that ran
+ * out) after synchronizing the device; returns AIDW_OK or AIDW_ERR_TIMEOUT and clears it. */
+int aidw_check_device_errors(aidw_ctx *ctx);
+
+/* Per-kernel device times of the most recent aidw_interpolate on this context, measured with
+ * CUDA events on the call's stream when profiling is on (aidw_set_profiling). */
+typedef struct aidw_kernel_times {
+    double knn_ms;      /* phase 1 distance scan and neighbour lists */
+    double select_ms;   /* neighbour-list merge and Eq. 2-6 */
+    double weights_ms;  /* phase 2 distance scan and weighted sums */
+    double finalize_ms; /* split merge and the ratio of Eq. 1 */
+    int32_t splits;     /* data-range splits of the phase-1 scan */
+    int32_t query_blocks;
+    int32_t launches;   /* kernels launched by the call */
+    int32_t weight_splits; /* data-range splits of the phase-2 scan */
+} aidw_kernel_times;
+
+int aidw_set_profiling(aidw_ctx *ctx, int on);
+int aidw_last_kernel_times(aidw_ctx *ctx, aidw_kernel_times *out);
+
+/* Measured issue rates of the pipes that bound the kernels, for roofline denominators:
+ * FP32 FFMA and MUFU ex2/lg2 results per clock per SM, timed by microbenchmark kernels on the
+ * context's device, plus the SM count and the SM clock the driver reports. */
+typedef struct aidw_pipe_rates {
+    double ffma_per_clk_sm;
+    double ex2_per_clk_sm;
+    double lg2_per_clk_sm;
+    double fmnmx_per_clk_sm;
+    double sm_clock_mhz; /* clock observed during the microbenchmarks */
+    int32_t sm_count;
+    int32_t reserved;
+} aidw_pipe_rates;
+
+int aidw_measure_pipe_rates(aidw_ctx *ctx, aidw_pipe_rates *out);
+
+/* Test hook (host-side fault injection): the `after`-th device allocation from now fails with
+ * AIDW_ERR_OOM; after < 0 disables it. */
+int aidw_debug_fail_alloc_after(aidw_ctx *ctx, int64_t after);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIDW_H */

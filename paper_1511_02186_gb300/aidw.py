@@ -1,0 +1,341 @@
+"""Python binding of ``libaidw.so`` (the C ABI in ``include/aidw.h``).
+
+Argument marshalling only: every step of the interpolation runs in the library's CUDA kernels.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA memory); torch provides
+device memory and streams, nothing else. If the compiled library is missing this module raises
+instead of falling back to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libaidw.so")
+
+OK = 0
+PENDING = 1
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_AGAIN = -3
+ERR_TIMEOUT = -4
+ERR_CUDA = -5
+ERR_NOT_FOUND = -6
+ERR_UNSUPPORTED = -7
+
+F32C = 0
+F64 = 1
+DTYPE_F32 = 0
+DTYPE_F64 = 1
+MAX_K = 32
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AidwError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+class Params(ctypes.Structure):
+    """``aidw_params``: k, precision, alpha levels (Eq. 6), R_min / R_max (Eq. 5)."""
+    _fields_ = [("k", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("alpha", ctypes.c_double * 5), ("r_min", ctypes.c_double),
+                ("r_max", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32)]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("knn_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
+                ("weights_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
+                ("splits", ctypes.c_int32), ("query_blocks", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("weight_splits", ctypes.c_int32)]
+
+
+class PipeRates(ctypes.Structure):
+    _fields_ = [("ffma_per_clk_sm", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
+                ("lg2_per_clk_sm", ctypes.c_double), ("fmnmx_per_clk_sm", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ds", ctypes.c_int64), ("qx", ctypes.c_void_p), ("qy", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("params", Params), ("out", ctypes.c_void_p),
+                ("out_alpha", ctypes.c_void_p)]
+
+
+# Every symbol of include/aidw.h with its signature (restype, argtypes).
+_P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "aidw_params_default": (None, [_P]),
+    "aidw_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_size_t]),
+    "aidw_shutdown": (ctypes.c_int, [_P]),
+    "aidw_create_dataset": (ctypes.c_int, [_P, _P, _P, _P, _I64, _D, _I32, _P]),
+    "aidw_destroy_dataset": (ctypes.c_int, [_P, _I64]),
+    "aidw_dataset_info": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "aidw_interpolate": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "aidw_idw": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _D, _I32, _P, _P]),
+    "aidw_interpolate_batch": (ctypes.c_int, [_P, _P, _I32, _P]),
+    "aidw_submit": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "aidw_poll": (ctypes.c_int, [_P, _I64, _P]),
+    "aidw_wait": (ctypes.c_int, [_P, _I64, _I64]),
+    "aidw_request_latency_us": (ctypes.c_int, [_P, _I64, _P]),
+    "aidw_release_request": (ctypes.c_int, [_P, _I64]),
+    "aidw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "aidw_check_device_errors": (ctypes.c_int, [_P]),
+    "aidw_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "aidw_last_kernel_times": (ctypes.c_int, [_P, _P]),
+    "aidw_measure_pipe_rates": (ctypes.c_int, [_P, _P]),
+    "aidw_debug_fail_alloc_after": (ctypes.c_int, [_P, _I64]),
+}
+# Test-only hooks exported by the library but not declared in the public header.
+DEBUG_SIGNATURES = {
+    "aidw_debug_interpolate_splits": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P,
+                                                     _I32, _I32]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libaidw.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in {**SIGNATURES, **DEBUG_SIGNATURES}.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    return load().aidw_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise AidwError(rc, what)
+
+
+def default_params(k: int = 10, levels=(1.0, 2.0, 3.0, 4.0, 5.0), r_min: float = 0.0,
+                   r_max: float = 2.0, precision: int = F32C) -> Params:
+    p = Params()
+    load().aidw_params_default(ctypes.byref(p))
+    p.k = int(k)
+    p.precision = int(precision)
+    for i, a in enumerate(levels):
+        p.alpha[i] = float(a)
+    p.r_min = float(r_min)
+    p.r_max = float(r_max)
+    return p
+
+
+# ---- array marshalling -------------------------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _prep(a, dtype):
+    """Returns (keepalive, pointer) for a 1-D contiguous array of `dtype` ('f4','f8','i4')."""
+    if _is_torch(a):
+        import torch
+        tdt = {"f4": torch.float32, "f8": torch.float64, "i4": torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor, got {a.dtype}")
+        return a, a.data_ptr()
+    arr = np.asarray(a)
+    if arr.dtype != np.dtype(dtype) or not arr.flags.c_contiguous:
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+    return arr, arr.ctypes.data
+
+
+def _out_like(q, shape, dtype):
+    if _is_torch(q):
+        import torch
+        tdt = {"f4": torch.float32, "f8": torch.float64, "i4": torch.int32}[dtype]
+        return torch.empty(shape, dtype=tdt, device=q.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _stream_of(a, stream):
+    if stream is not None:
+        return int(stream)
+    if _is_torch(a) and a.is_cuda:
+        import torch
+        return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+class Dataset:
+    def __init__(self, ctx: "Context", handle: int, n: int, area: float):
+        self.ctx, self.handle, self.n, self.area = ctx, handle, n, area
+
+    def destroy(self):
+        if self.handle:
+            _check(self.ctx.lib.aidw_destroy_dataset(self.ctx.ptr, self.handle), "destroy")
+            self.handle = 0
+
+
+class Context:
+    """One library context on one CUDA device (``aidw_init`` / ``aidw_shutdown``)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = load()
+        self._ptr = ctypes.c_void_p()
+        _check(self.lib.aidw_init(ctypes.byref(self._ptr), int(device), int(hbm_budget)),
+               "aidw_init")
+        self.device = device
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("context is closed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr:
+            self.lib.aidw_shutdown(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- datasets --
+    def create_dataset(self, x, y, z, area: float, dtype: str = "f8") -> Dataset:
+        kx, px = _prep(x, dtype)
+        ky, py = _prep(y, dtype)
+        kz, pz = _prep(z, dtype)
+        n = int(kx.shape[0])
+        h = ctypes.c_int64()
+        _check(self.lib.aidw_create_dataset(self.ptr, px, py, pz, n, float(area),
+                                            DTYPE_F64 if dtype == "f8" else DTYPE_F32,
+                                            ctypes.byref(h)), "aidw_create_dataset")
+        return Dataset(self, h.value, n, area)
+
+    # -- one-shot interpolation --
+    def interpolate(self, ds: Dataset, qx, qy, params: Params | None = None, out=None,
+                    out_alpha=None, out_knn=None, want_alpha=False, want_knn=False,
+                    stream=None, splits=None):
+        """AIDW at the queries; returns (out, out_alpha or None, out_knn or None)."""
+        p = params or default_params()
+        fdt = "f8" if p.precision == F64 else "f4"
+        kqx, pqx = _prep(qx, fdt)
+        kqy, pqy = _prep(qy, fdt)
+        m = int(kqx.shape[0])
+        if out is None:
+            out = _out_like(qx, (m,), fdt)
+        if want_alpha and out_alpha is None:
+            out_alpha = _out_like(qx, (m,), "f4")
+        if want_knn and out_knn is None:
+            out_knn = _out_like(qx, (m, p.k), "i4")
+        ko, po = _prep(out, fdt)
+        ka, pa = (None, None) if out_alpha is None else _prep(out_alpha, "f4")
+        kn, pn = (None, None) if out_knn is None else _prep(out_knn, "i4")
+        st = _stream_of(qx, stream)
+        if splits is None:
+            rc = self.lib.aidw_interpolate(self.ptr, ds.handle, pqx, pqy, m, ctypes.byref(p),
+                                           po, pa, pn, st)
+        else:
+            rc = self.lib.aidw_debug_interpolate_splits(self.ptr, ds.handle, pqx, pqy, m,
+                                                        ctypes.byref(p), po, pa, pn, st,
+                                                        int(splits[0]), int(splits[1]))
+        _check(rc, "aidw_interpolate")
+        for keep, res in ((ko, out), (ka, out_alpha), (kn, out_knn)):
+            if keep is not None and keep is not res and isinstance(res, np.ndarray):
+                res[...] = keep
+        return out, out_alpha, out_knn
+
+    def idw(self, ds: Dataset, qx, qy, alpha: float, precision: int = F32C, out=None,
+            stream=None):
+        fdt = "f8" if precision == F64 else "f4"
+        kqx, pqx = _prep(qx, fdt)
+        kqy, pqy = _prep(qy, fdt)
+        m = int(kqx.shape[0])
+        if out is None:
+            out = _out_like(qx, (m,), fdt)
+        ko, po = _prep(out, fdt)
+        _check(self.lib.aidw_idw(self.ptr, ds.handle, pqx, pqy, m, float(alpha), int(precision),
+                                 po, _stream_of(qx, stream)), "aidw_idw")
+        return out
+
+    def interpolate_batch(self, items, stream=None):
+        """items: list of (Dataset, qx, qy, Params, out, out_alpha|None) with CUDA tensors."""
+        arr = (BatchItem * len(items))()
+        keep = []
+        for i, (ds, qx, qy, p, out, oa) in enumerate(items):
+            arr[i].ds = ds.handle
+            arr[i].qx = qx.data_ptr()
+            arr[i].qy = qy.data_ptr()
+            arr[i].m = int(qx.shape[0])
+            arr[i].params = p
+            arr[i].out = out.data_ptr()
+            arr[i].out_alpha = oa.data_ptr() if oa is not None else None
+            keep.append((qx, qy, out, oa))
+        st = _stream_of(items[0][1], stream) if items else 0
+        _check(self.lib.aidw_interpolate_batch(self.ptr, arr, len(items), st),
+               "aidw_interpolate_batch")
+
+    # -- serving --
+    def submit(self, ds: Dataset, qx, qy, params: Params, out, out_alpha=None, out_knn=None):
+        fdt = "f8" if params.precision == F64 else "f4"
+        _, pqx = _prep(qx, fdt)
+        _, pqy = _prep(qy, fdt)
+        _, po = _prep(out, fdt)
+        pa = None if out_alpha is None else _prep(out_alpha, "f4")[1]
+        pn = None if out_knn is None else _prep(out_knn, "i4")[1]
+        rid = ctypes.c_int64()
+        rc = self.lib.aidw_submit(self.ptr, ds.handle, pqx, pqy, int(len(qx)),
+                                  ctypes.byref(params), po, pa, pn, ctypes.byref(rid))
+        return rc, rid.value
+
+    def poll(self, rid: int):
+        d = ctypes.c_int32()
+        rc = self.lib.aidw_poll(self.ptr, int(rid), ctypes.byref(d))
+        return rc, bool(d.value)
+
+    def wait(self, rid: int, timeout_us: int = -1) -> int:
+        return self.lib.aidw_wait(self.ptr, int(rid), int(timeout_us))
+
+    def latency_us(self, rid: int) -> float:
+        v = ctypes.c_double()
+        _check(self.lib.aidw_request_latency_us(self.ptr, int(rid), ctypes.byref(v)), "latency")
+        return v.value
+
+    def release(self, rid: int) -> int:
+        return self.lib.aidw_release_request(self.ptr, int(rid))
+
+    # -- diagnostics --
+    def set_profiling(self, on: bool):
+        _check(self.lib.aidw_set_profiling(self.ptr, 1 if on else 0), "set_profiling")
+
+    def kernel_times(self) -> KernelTimes:
+        t = KernelTimes()
+        _check(self.lib.aidw_last_kernel_times(self.ptr, ctypes.byref(t)), "kernel_times")
+        return t
+
+    def pipe_rates(self) -> PipeRates:
+        r = PipeRates()
+        _check(self.lib.aidw_measure_pipe_rates(self.ptr, ctypes.byref(r)), "pipe_rates")
+        return r
+
+    def check_device_errors(self) -> int:
+        return self.lib.aidw_check_device_errors(self.ptr)
+
+    def fail_alloc_after(self, n: int):
+        _check(self.lib.aidw_debug_fail_alloc_after(self.ptr, int(n)), "fail_alloc_after")

@@ -1,0 +1,866 @@
+// C ABI of the library: context, dataset store, one-shot interpolation, diagnostics.
+// The batched and serving entry points live in runtime.cu.
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "aidw_internal.cuh"
+#include "aidw_runtime.h"
+
+namespace aidw {
+
+namespace {
+
+inline size_t align256(size_t b)
+{
+    return (b + 255) & ~static_cast<size_t>(255);
+}
+
+// Converts caller arrays (float or double) into the four padded device layouts and counts
+// non-finite inputs. Padding points are +inf with value 0.
+template <typename T>
+__global__ void convert_dataset_kernel(const T *__restrict__ x, const T *__restrict__ y,
+                                       const T *__restrict__ z, int64_t n, int64_t n_pad,
+                                       float2 *xy, float4 *xyzw, double2 *xy64, double *z64,
+                                       unsigned long long *bad)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    unsigned long long nb = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_pad;
+         i += stride) {
+        double a, b, c;
+        if (i < n) {
+            a = static_cast<double>(x[i]);
+            b = static_cast<double>(y[i]);
+            c = static_cast<double>(z[i]);
+            nb += (isfinite(a) && isfinite(b) && isfinite(c)) ? 0 : 1;
+        } else {
+            a = b = CUDART_INF;
+            c = 0.0;
+        }
+        const float fa = static_cast<float>(a), fb = static_cast<float>(b);
+        const float fc = static_cast<float>(c);
+        // FP32 copies must stay finite too (coordinates beyond float range are rejected).
+        if (i < n && !(isfinite(fa) && isfinite(fb) && isfinite(fc)))
+            ++nb;
+        xy[i] = make_float2(fa, fb);
+        xyzw[i] = make_float4(fa, fb, fc, 0.0f);
+        xy64[i] = make_double2(a, b);
+        z64[i] = c;
+    }
+    if (nb)
+        atomicAdd(bad, nb);
+}
+
+}  // namespace
+
+}  // namespace aidw
+
+using namespace aidw;
+
+struct DatasetRec {
+    DatasetDev dev;
+    void *block = nullptr;
+    size_t bytes = 0;
+    double area = 0.0;
+    double r_exp = 0.0;
+};
+
+struct aidw_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int64_t fail_after = -1;
+    int *d_err = nullptr;
+    unsigned long long *d_bad = nullptr;
+    cudaMemPool_t pool = nullptr;
+    std::mutex mu;
+    std::unordered_map<int64_t, DatasetRec> datasets;
+    int64_t next_ds = 1;
+    bool profiling = false;
+    cudaEvent_t ev[5] = {};
+    aidw_kernel_times last{};
+    bool last_valid = false;
+    int slots_cache[2][3][2] = {};  // [precision][kp bucket][with_idx] knn slots
+    int wslots_cache[2] = {};
+    ServingRuntime *serving = nullptr;
+};
+
+namespace aidw {
+
+// ---- memory accounting --------------------------------------------------------------------
+
+int ctx_alloc(aidw_ctx *ctx, size_t bytes, cudaStream_t st, void **p)
+{
+    *p = nullptr;
+    if (bytes == 0)
+        return AIDW_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->fail_after >= 0) {
+            if (ctx->fail_after == 0) {
+                ctx->fail_after = -1;
+                return AIDW_ERR_OOM;
+            }
+            --ctx->fail_after;
+        }
+        if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+            return AIDW_ERR_OOM;
+        ctx->in_use += bytes;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->in_use -= bytes;
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? AIDW_ERR_OOM : AIDW_ERR_CUDA;
+    }
+    return AIDW_OK;
+}
+
+void ctx_free(aidw_ctx *ctx, void *p, size_t bytes, cudaStream_t st)
+{
+    if (!p)
+        return;
+    cudaFreeAsync(p, st);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->in_use -= bytes;
+}
+
+size_t ctx_budget_left(aidw_ctx *ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->budget)
+        return SIZE_MAX;
+    return ctx->budget > ctx->in_use ? ctx->budget - ctx->in_use : 0;
+}
+
+int *ctx_err_word(aidw_ctx *ctx)
+{
+    return ctx->d_err;
+}
+
+int ctx_device(aidw_ctx *ctx)
+{
+    return ctx->device;
+}
+
+int ctx_sm_count(aidw_ctx *ctx)
+{
+    return ctx->sm_count;
+}
+
+const DatasetRec *ctx_dataset(aidw_ctx *ctx, aidw_dataset id)
+{
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->datasets.find(id);
+    return it == ctx->datasets.end() ? nullptr : &it->second;
+}
+
+bool dataset_lookup(aidw_ctx *ctx, aidw_dataset id, DatasetDev *dev, double *r_exp)
+{
+    const DatasetRec *r = ctx_dataset(ctx, id);
+    if (!r)
+        return false;
+    *dev = r->dev;
+    *r_exp = r->r_exp;
+    return true;
+}
+
+// ---- pointers ----------------------------------------------------------------------------
+
+// 1: device memory of `device`; 0: host memory; -1: device memory of another device.
+int pointer_kind(const void *p, int device)
+{
+    if (!p)
+        return 0;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == device ? 1 : -1;
+    return 0;
+}
+
+// ---- planning ------------------------------------------------------------------------------
+
+static PassPlan plan_pass(int64_t m, int64_t n_pad, int qpb, int slots_total, int64_t fixed)
+{
+    PassPlan pp{};
+    pp.q_per_block = qpb;
+    pp.qblocks = static_cast<int>((m + qpb - 1) / qpb);
+    const int64_t G = n_pad / kPadPoints;
+    double best = 1e300;
+    for (int S = 1; S <= kMaxSplits && S <= G; ++S) {
+        const int64_t per = (G + S - 1) / S;
+        const int64_t Se = (G + per - 1) / per;
+        if (Se != S)
+            continue;
+        const int64_t items = static_cast<int64_t>(pp.qblocks) * Se;
+        const int64_t waves = (items + slots_total - 1) / slots_total;
+        const double cost = static_cast<double>(waves) * (per * kPadPoints + fixed);
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            pp.splits = static_cast<int>(Se);
+            pp.split_len = per * kPadPoints;
+        }
+    }
+    return pp;
+}
+
+static int kp_bucket(int k)
+{
+    return k <= 8 ? 0 : (k <= 16 ? 1 : 2);
+}
+
+Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bool with_idx,
+               int force_knn_splits, int force_w_splits)
+{
+    int &ks = ctx->slots_cache[precision][kp_bucket(k)][with_idx ? 1 : 0];
+    if (!ks)
+        ks = precision == AIDW_F64 ? f64_knn_slots_per_sm(k, with_idx)
+                                   : f32_knn_slots_per_sm(k, with_idx);
+    int &ws = ctx->wslots_cache[precision];
+    if (!ws)
+        ws = precision == AIDW_F64 ? f64_w_slots_per_sm() : f32_w_slots_per_sm();
+    Plan pl{};
+    pl.m = m;
+    pl.with_idx = with_idx;
+    const int qk = precision == AIDW_F64 ? f64_knn_queries_per_block(k)
+                                         : f32_knn_queries_per_block(k);
+    const int qw = precision == AIDW_F64 ? f64_w_queries_per_block() : f32_w_queries_per_block();
+    // A split restarts its neighbour lists, costing about k log(n/k) insertions per query;
+    // it is charged as a few thousand points of scan.
+    pl.knn = plan_pass(m, n_pad, qk, ks * ctx->sm_count, 4096 + 256 * k);
+    pl.w = plan_pass(m, n_pad, qw, ws * ctx->sm_count, 1024);
+    const int64_t G = n_pad / kPadPoints;
+    auto force = [&](PassPlan &pp, int S) {
+        if (S <= 0)
+            return;
+        S = static_cast<int>(S > G ? G : S);
+        S = S > kMaxSplits ? kMaxSplits : S;
+        const int64_t per = (G + S - 1) / S;
+        pp.splits = static_cast<int>((G + per - 1) / per);
+        pp.split_len = per * kPadPoints;
+    };
+    force(pl.knn, force_knn_splits);
+    force(pl.w, force_w_splits);
+    return pl;
+}
+
+size_t scratch_bytes(int precision, const Plan &pl, int k)
+{
+    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    const size_t m = static_cast<size_t>(pl.m);
+    size_t b = align256(pl.knn.splits * static_cast<size_t>(k) * m * es);
+    if (pl.with_idx)
+        b += align256(pl.knn.splits * static_cast<size_t>(k) * m * sizeof(int32_t));
+    b += align256(m * (precision == AIDW_F64 ? sizeof(QParamF64) : sizeof(QParamF32)));
+    b += align256(pl.w.splits * 4 * m * es);
+    return b;
+}
+
+void scratch_carve(void *base, int precision, const Plan &pl, int k, Scratch *s)
+{
+    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    const size_t m = static_cast<size_t>(pl.m);
+    char *p = static_cast<char *>(base);
+    s->part_d2 = p;
+    p += align256(pl.knn.splits * static_cast<size_t>(k) * m * es);
+    s->part_idx = nullptr;
+    if (pl.with_idx) {
+        s->part_idx = reinterpret_cast<int32_t *>(p);
+        p += align256(pl.knn.splits * static_cast<size_t>(k) * m * sizeof(int32_t));
+    }
+    s->qparam = p;
+    p += align256(m * (precision == AIDW_F64 ? sizeof(QParamF64) : sizeof(QParamF32)));
+    s->part_sum = p;
+}
+
+int validate_params(const aidw_params *p, int64_t n)
+{
+    if (!p)
+        return AIDW_ERR_INVALID_ARG;
+    if (p->precision != AIDW_F32C && p->precision != AIDW_F64)
+        return AIDW_ERR_INVALID_ARG;
+    if (p->k < 1 || p->k > AIDW_MAX_K || p->k > n)
+        return AIDW_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (!std::isfinite(p->alpha[i]) || !(p->alpha[i] > 0.0))
+            return AIDW_ERR_INVALID_ARG;
+    if (!std::isfinite(p->r_min) || !std::isfinite(p->r_max) || !(p->r_max > p->r_min) ||
+        !(p->r_max > 0.0))
+        return AIDW_ERR_INVALID_ARG;
+    if (p->flags != 0 || p->reserved != 0)
+        return AIDW_ERR_INVALID_ARG;
+    return AIDW_OK;
+}
+
+AlphaMap alpha_map(const aidw_params &p)
+{
+    AlphaMap am;
+    for (int i = 0; i < 5; ++i)
+        am.level[i] = p.alpha[i];
+    am.r_min = p.r_min;
+    am.r_max = p.r_max;
+    return am;
+}
+
+// Enqueues the four kernels of one interpolation on `st` with device arrays only.
+int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
+                          const aidw_params &p, const void *qx, const void *qy,
+                          const Scratch &sc, void *out, float *out_alpha, int32_t *out_knn,
+                          cudaStream_t st, bool profile)
+{
+    const AlphaMap am = alpha_map(p);
+    cudaError_t e;
+    const bool f64 = p.precision == AIDW_F64;
+    if (profile)
+        cudaEventRecord(ctx->ev[0], st);
+    e = f64 ? launch_f64_knn(ds, pl, static_cast<const double *>(qx),
+                             static_cast<const double *>(qy), p.k, sc, ctx->d_err, st)
+            : launch_f32_knn(ds, pl, static_cast<const float *>(qx),
+                             static_cast<const float *>(qy), p.k, sc, ctx->d_err, st);
+    if (e != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (profile)
+        cudaEventRecord(ctx->ev[1], st);
+    e = f64 ? launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st)
+            : launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st);
+    if (e != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (profile)
+        cudaEventRecord(ctx->ev[2], st);
+    e = f64 ? launch_f64_weights(ds, pl, static_cast<const double *>(qx),
+                                 static_cast<const double *>(qy), sc, ctx->d_err, st)
+            : launch_f32_weights(ds, pl, static_cast<const float *>(qx),
+                                 static_cast<const float *>(qy), sc, ctx->d_err, st);
+    if (e != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (profile)
+        cudaEventRecord(ctx->ev[3], st);
+    e = f64 ? launch_f64_finalize(pl, sc, static_cast<double *>(out), st)
+            : launch_f32_finalize(pl, sc, static_cast<float *>(out), st);
+    if (e != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (profile) {
+        cudaEventRecord(ctx->ev[4], st);
+        ctx->last = aidw_kernel_times{};
+        ctx->last.splits = pl.knn.splits;
+        ctx->last.query_blocks = pl.knn.qblocks;
+        ctx->last.launches = 4;
+        ctx->last.weight_splits = pl.w.splits;
+        ctx->last_valid = true;
+    }
+    return AIDW_OK;
+}
+
+// Reads and clears the on-device error word (synchronous).
+int consume_device_error(aidw_ctx *ctx, cudaStream_t st)
+{
+    int h = 0;
+    if (cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (h) {
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        return AIDW_ERR_TIMEOUT;
+    }
+    return AIDW_OK;
+}
+
+// Full interpolation, host or device arrays (see aidw.h). `force_*` override the split
+// counts (used by the tests to exercise split merges); 0 means "plan".
+int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const void *qy,
+                     int64_t m, const aidw_params *p, void *out, float *out_alpha,
+                     int32_t *out_knn, cudaStream_t st, int force_knn_splits,
+                     int force_w_splits)
+{
+    DatasetDev ds;
+    double r_exp;
+    if (!dataset_lookup(ctx, dsid, &ds, &r_exp))
+        return AIDW_ERR_NOT_FOUND;
+    int rc = validate_params(p, ds.n);
+    if (rc)
+        return rc;
+    if (m < 0 || m > (int64_t(1) << 31))
+        return AIDW_ERR_INVALID_ARG;
+    if (m == 0)
+        return AIDW_OK;
+    if (!qx || !qy || !out)
+        return AIDW_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    const bool f64 = p->precision == AIDW_F64;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const int kq = pointer_kind(qx, ctx->device), kqy = pointer_kind(qy, ctx->device);
+    const int ko = pointer_kind(out, ctx->device);
+    const int ka = pointer_kind(out_alpha, ctx->device);
+    const int kn = pointer_kind(out_knn, ctx->device);
+    if (kq < 0 || kqy < 0 || ko < 0 || ka < 0 || kn < 0)
+        return AIDW_ERR_INVALID_ARG;
+    const bool host_q = kq == 0 || kqy == 0;
+    const bool host_any = host_q || ko == 0 || (out_alpha && ka == 0) || (out_knn && kn == 0);
+    if (host_q) {
+        for (int64_t i = 0; i < m; ++i) {
+            const double a = f64 ? static_cast<const double *>(qx)[i]
+                                 : static_cast<const float *>(qx)[i];
+            const double b = f64 ? static_cast<const double *>(qy)[i]
+                                 : static_cast<const float *>(qy)[i];
+            if (!std::isfinite(a) || !std::isfinite(b))
+                return AIDW_ERR_INVALID_ARG;
+        }
+    }
+
+    const Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
+                              force_knn_splits, force_w_splits);
+    const size_t sb = scratch_bytes(p->precision, pl, p->k);
+    // Staging for host arrays.
+    const size_t b_q = (kq == 0 ? align256(m * es) : 0) + (kqy == 0 ? align256(m * es) : 0);
+    const size_t b_o = ko == 0 ? align256(m * es) : 0;
+    const size_t b_a = (out_alpha && ka == 0) ? align256(m * sizeof(float)) : 0;
+    const size_t b_n = (out_knn && kn == 0) ? align256(m * p->k * sizeof(int32_t)) : 0;
+    const size_t total = sb + b_q + b_o + b_a + b_n;
+    void *blk = nullptr;
+    rc = ctx_alloc(ctx, total, st, &blk);
+    if (rc)
+        return rc;
+    Scratch sc;
+    scratch_carve(blk, p->precision, pl, p->k, &sc);
+    char *stage = static_cast<char *>(blk) + sb;
+    const void *dqx = qx, *dqy = qy;
+    void *dout = out;
+    float *dalpha = out_alpha;
+    int32_t *dknn = out_knn;
+    bool ok = true;
+    if (kq == 0) {
+        ok &= cudaMemcpyAsync(stage, qx, m * es, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        dqx = stage;
+        stage += align256(m * es);
+    }
+    if (kqy == 0) {
+        ok &= cudaMemcpyAsync(stage, qy, m * es, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        dqy = stage;
+        stage += align256(m * es);
+    }
+    if (ko == 0) {
+        dout = stage;
+        stage += b_o;
+    }
+    if (out_alpha && ka == 0) {
+        dalpha = reinterpret_cast<float *>(stage);
+        stage += b_a;
+    }
+    if (out_knn && kn == 0) {
+        dknn = reinterpret_cast<int32_t *>(stage);
+        stage += b_n;
+    }
+    if (!ok) {
+        ctx_free(ctx, blk, total, st);
+        return AIDW_ERR_CUDA;
+    }
+    rc = enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn, st,
+                               ctx->profiling);
+    if (rc == AIDW_OK && host_any) {
+        ok = true;
+        if (ko == 0)
+            ok &= cudaMemcpyAsync(out, dout, m * es, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (out_alpha && ka == 0)
+            ok &= cudaMemcpyAsync(out_alpha, dalpha, m * sizeof(float), cudaMemcpyDeviceToHost,
+                                  st) == cudaSuccess;
+        if (out_knn && kn == 0)
+            ok &= cudaMemcpyAsync(out_knn, dknn, m * p->k * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (!ok)
+            rc = AIDW_ERR_CUDA;
+    }
+    ctx_free(ctx, blk, total, st);
+    if (rc == AIDW_OK && host_any)
+        rc = consume_device_error(ctx, st);
+    return rc;
+}
+
+}  // namespace aidw
+
+// =============================================================================================
+// extern "C" entry points
+// =============================================================================================
+
+extern "C" {
+
+void aidw_params_default(aidw_params *p)
+{
+    if (!p)
+        return;
+    std::memset(p, 0, sizeof(*p));
+    p->k = 10;
+    p->precision = AIDW_F32C;
+    for (int i = 0; i < 5; ++i)
+        p->alpha[i] = 1.0 + i;
+    p->r_min = 0.0;
+    p->r_max = 2.0;
+}
+
+const char *aidw_status_string(int s)
+{
+    switch (s) {
+    case AIDW_OK: return "ok";
+    case AIDW_PENDING: return "pending";
+    case AIDW_ERR_INVALID_ARG: return "invalid argument";
+    case AIDW_ERR_OOM: return "out of device memory or HBM budget";
+    case AIDW_ERR_AGAIN: return "queue full, try again";
+    case AIDW_ERR_TIMEOUT: return "timed out";
+    case AIDW_ERR_CUDA: return "CUDA runtime error";
+    case AIDW_ERR_NOT_FOUND: return "unknown handle";
+    case AIDW_ERR_UNSUPPORTED: return "unsupported device or option";
+    default: return "unknown status";
+    }
+}
+
+int aidw_init(aidw_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out)
+        return AIDW_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return AIDW_ERR_INVALID_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3)
+        return AIDW_ERR_UNSUPPORTED;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    aidw_ctx *ctx = new aidw_ctx();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->budget = hbm_budget_bytes;
+    cudaMemPoolProps pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    bool ok = cudaMemPoolCreate(&ctx->pool, &pp) == cudaSuccess;
+    if (ok) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    ok = ok && cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->d_bad, sizeof(unsigned long long)) == cudaSuccess;
+    ok = ok && cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess;
+    for (int i = 0; ok && i < 5; ++i)
+        ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        aidw_shutdown(ctx);
+        return AIDW_ERR_CUDA;
+    }
+    *out = ctx;
+    return AIDW_OK;
+}
+
+int aidw_shutdown(aidw_ctx *ctx)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    serving_stop(ctx->serving);
+    ctx->serving = nullptr;
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->datasets)
+        cudaFree(kv.second.block);
+    ctx->datasets.clear();
+    if (ctx->d_err)
+        cudaFree(ctx->d_err);
+    if (ctx->d_bad)
+        cudaFree(ctx->d_bad);
+    for (int i = 0; i < 5; ++i)
+        if (ctx->ev[i])
+            cudaEventDestroy(ctx->ev[i]);
+    if (ctx->pool)
+        cudaMemPoolDestroy(ctx->pool);
+    cudaGetLastError();
+    delete ctx;
+    return AIDW_OK;
+}
+
+int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void *z, int64_t n,
+                        double area, int32_t dtype, aidw_dataset *out)
+{
+    if (!ctx || !x || !y || !z || !out)
+        return AIDW_ERR_INVALID_ARG;
+    *out = 0;
+    if (n < 1 || n > (int64_t(1) << 31) - 2 * kPadPoints)
+        return AIDW_ERR_INVALID_ARG;
+    if (!std::isfinite(area) || !(area > 0.0))
+        return AIDW_ERR_INVALID_ARG;
+    if (dtype != AIDW_DTYPE_F32 && dtype != AIDW_DTYPE_F64)
+        return AIDW_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    const int kx = pointer_kind(x, ctx->device), ky = pointer_kind(y, ctx->device);
+    const int kz = pointer_kind(z, ctx->device);
+    if (kx < 0 || ky < 0 || kz < 0)
+        return AIDW_ERR_INVALID_ARG;
+    const size_t es = dtype == AIDW_DTYPE_F64 ? sizeof(double) : sizeof(float);
+    const int64_t n_pad = (n + kPadPoints - 1) / kPadPoints * kPadPoints;
+    const size_t np = static_cast<size_t>(n_pad);
+    const size_t bytes = align256(np * sizeof(float2)) + align256(np * sizeof(float4)) +
+                         align256(np * sizeof(double2)) + align256(np * sizeof(double));
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->fail_after >= 0) {
+            if (ctx->fail_after == 0) {
+                ctx->fail_after = -1;
+                return AIDW_ERR_OOM;
+            }
+            --ctx->fail_after;
+        }
+        if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+            return AIDW_ERR_OOM;
+        ctx->in_use += bytes;
+    }
+    auto unreserve = [&]() {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->in_use -= bytes;
+    };
+    void *blk = nullptr;
+    if (cudaMalloc(&blk, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        unreserve();
+        return AIDW_ERR_OOM;
+    }
+    // Stage host arrays.
+    void *stage = nullptr;
+    const void *sx = x, *sy = y, *sz = z;
+    const size_t one = align256(static_cast<size_t>(n) * es);
+    int rc = AIDW_OK;
+    if (kx == 0 || ky == 0 || kz == 0) {
+        if (cudaMalloc(&stage, 3 * one) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(blk);
+            unreserve();
+            return AIDW_ERR_OOM;
+        }
+        char *s = static_cast<char *>(stage);
+        if (kx == 0) {
+            cudaMemcpy(s, x, n * es, cudaMemcpyHostToDevice);
+            sx = s;
+        }
+        if (ky == 0) {
+            cudaMemcpy(s + one, y, n * es, cudaMemcpyHostToDevice);
+            sy = s + one;
+        }
+        if (kz == 0) {
+            cudaMemcpy(s + 2 * one, z, n * es, cudaMemcpyHostToDevice);
+            sz = s + 2 * one;
+        }
+    }
+    DatasetRec rec;
+    char *b = static_cast<char *>(blk);
+    float2 *xy = reinterpret_cast<float2 *>(b);
+    b += align256(np * sizeof(float2));
+    float4 *xyzw = reinterpret_cast<float4 *>(b);
+    b += align256(np * sizeof(float4));
+    double2 *xy64 = reinterpret_cast<double2 *>(b);
+    b += align256(np * sizeof(double2));
+    double *z64 = reinterpret_cast<double *>(b);
+    cudaMemset(ctx->d_bad, 0, sizeof(unsigned long long));
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<int64_t>((n_pad + threads - 1) / threads,
+                                                          ctx->sm_count * 8));
+    if (dtype == AIDW_DTYPE_F64)
+        convert_dataset_kernel<double><<<blocks, threads>>>(
+            static_cast<const double *>(sx), static_cast<const double *>(sy),
+            static_cast<const double *>(sz), n, n_pad, xy, xyzw, xy64, z64, ctx->d_bad);
+    else
+        convert_dataset_kernel<float><<<blocks, threads>>>(
+            static_cast<const float *>(sx), static_cast<const float *>(sy),
+            static_cast<const float *>(sz), n, n_pad, xy, xyzw, xy64, z64, ctx->d_bad);
+    unsigned long long bad = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(&bad, ctx->d_bad, sizeof(bad), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = AIDW_ERR_CUDA;
+    else if (bad)
+        rc = AIDW_ERR_INVALID_ARG;
+    if (stage)
+        cudaFree(stage);
+    if (rc) {
+        cudaFree(blk);
+        unreserve();
+        return rc;
+    }
+    rec.dev.xy = xy;
+    rec.dev.xyzw = xyzw;
+    rec.dev.xy64 = xy64;
+    rec.dev.z64 = z64;
+    rec.dev.n = n;
+    rec.dev.n_pad = n_pad;
+    rec.block = blk;
+    rec.bytes = bytes;
+    rec.area = area;
+    rec.r_exp = 1.0 / (2.0 * std::sqrt(static_cast<double>(n) / area));  // Eq. 2
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const int64_t id = ctx->next_ds++;
+    ctx->datasets.emplace(id, rec);
+    *out = id;
+    return AIDW_OK;
+}
+
+int aidw_destroy_dataset(aidw_ctx *ctx, aidw_dataset ds)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    DatasetRec rec;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->datasets.find(ds);
+        if (it == ctx->datasets.end())
+            return AIDW_ERR_NOT_FOUND;
+        rec = it->second;
+        ctx->datasets.erase(it);
+    }
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(rec.block);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->in_use -= rec.bytes;
+    return AIDW_OK;
+}
+
+int aidw_dataset_info(aidw_ctx *ctx, aidw_dataset ds, int64_t *n, size_t *device_bytes)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    const DatasetRec *r = ctx_dataset(ctx, ds);
+    if (!r)
+        return AIDW_ERR_NOT_FOUND;
+    if (n)
+        *n = r->dev.n;
+    if (device_bytes)
+        *device_bytes = r->bytes;
+    return AIDW_OK;
+}
+
+int aidw_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
+                     const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
+                     void *stream)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    return interpolate_impl(ctx, ds, qx, qy, m, p, out, out_alpha, out_knn,
+                            static_cast<cudaStream_t>(stream), 0, 0);
+}
+
+// Test hook with forced split counts (not part of the public header's contract).
+int aidw_debug_interpolate_splits(aidw_ctx *ctx, aidw_dataset ds, const void *qx,
+                                  const void *qy, int64_t m, const aidw_params *p, void *out,
+                                  float *out_alpha, int32_t *out_knn, void *stream,
+                                  int32_t knn_splits, int32_t w_splits)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    return interpolate_impl(ctx, ds, qx, qy, m, p, out, out_alpha, out_knn,
+                            static_cast<cudaStream_t>(stream), knn_splits, w_splits);
+}
+
+int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
+             double alpha, int32_t precision, void *out, void *stream)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    // Standard IDW is AIDW with five equal levels: Eq. 6 then returns alpha whatever R is.
+    // One neighbour is still found, to normalise the weights and to detect coincidence.
+    aidw_params p;
+    aidw_params_default(&p);
+    p.k = 1;
+    p.precision = precision;
+    for (int i = 0; i < 5; ++i)
+        p.alpha[i] = alpha;
+    return interpolate_impl(ctx, ds, qx, qy, m, &p, out, nullptr, nullptr,
+                            static_cast<cudaStream_t>(stream), 0, 0);
+}
+
+int aidw_check_device_errors(aidw_ctx *ctx)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    return consume_device_error(ctx, 0);
+}
+
+int aidw_set_profiling(aidw_ctx *ctx, int on)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    ctx->profiling = on != 0;
+    ctx->last_valid = false;
+    return AIDW_OK;
+}
+
+int aidw_last_kernel_times(aidw_ctx *ctx, aidw_kernel_times *out)
+{
+    if (!ctx || !out)
+        return AIDW_ERR_INVALID_ARG;
+    if (!ctx->last_valid)
+        return AIDW_ERR_NOT_FOUND;
+    if (cudaEventSynchronize(ctx->ev[4]) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    float t[4];
+    for (int i = 0; i < 4; ++i)
+        cudaEventElapsedTime(&t[i], ctx->ev[i], ctx->ev[i + 1]);
+    ctx->last.knn_ms = t[0];
+    ctx->last.select_ms = t[1];
+    ctx->last.weights_ms = t[2];
+    ctx->last.finalize_ms = t[3];
+    *out = ctx->last;
+    return AIDW_OK;
+}
+
+int aidw_measure_pipe_rates(aidw_ctx *ctx, aidw_pipe_rates *out)
+{
+    if (!ctx || !out)
+        return AIDW_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    return run_pipe_probe(ctx->sm_count, out) == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
+}
+
+int aidw_debug_fail_alloc_after(aidw_ctx *ctx, int64_t after)
+{
+    if (!ctx)
+        return AIDW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->fail_after = after < 0 ? -1 : after;
+    return AIDW_OK;
+}
+
+}  // extern "C"
+
+namespace aidw {
+ServingRuntime *&ctx_serving(aidw_ctx *ctx)
+{
+    return ctx->serving;
+}
+std::mutex &ctx_mutex(aidw_ctx *ctx)
+{
+    return ctx->mu;
+}
+}  // namespace aidw

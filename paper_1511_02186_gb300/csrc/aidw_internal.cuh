@@ -1,0 +1,245 @@
+// Internal declarations shared by the library's translation units: device-side dataset view,
+// launch plans, Blackwell TMA/mbarrier helpers and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/aidw.h"
+
+namespace aidw {
+
+// Data points per shared-memory tile. Dataset arrays are padded to a multiple of
+// kPadPoints with sentinel points at +infinity (value 0), which never enter a neighbour list
+// and get weight 0, so every tile is full and every TMA copy has a whole-tile size.
+constexpr int kTileF32Knn = 1024;  // float2 (x, y): 8 KiB per buffer
+constexpr int kTileF32W = 512;     // float4 (x, y, z, 0): 8 KiB per buffer
+constexpr int kTileF64Knn = 512;   // double2 (x, y): 8 KiB per buffer
+constexpr int kTileF64W = 512;     // double2 + double: 12 KiB per buffer
+constexpr int kPadPoints = 2048;   // common multiple of every tile and split granule
+
+// Added under the square of distances: it is absorbed (below half an ulp) for any distance
+// above ~1e-15 of unit scale, and turns an exact coincidence (d2 == 0) into d2 == kEps so
+// that log2 stays finite. FLT_MIN / DBL_MIN, the smallest normal numbers.
+constexpr float kEpsF32 = 1.17549435e-38f;
+constexpr double kEpsF64 = 2.2250738585072014e-308;
+// Power scale used for coincident queries: w = 2^(kCoincScale (L1 - log2 d2)) is exactly 1 on
+// a coincident point (d2 == eps) and underflows to 0 everywhere else.
+constexpr float kCoincScaleF32 = 1.2676506e30f;  // 2^100
+constexpr double kCoincScaleF64 = 8.452712498170644e270;  // 2^900
+
+// Bounded waits: an mbarrier wait gives up after this many polls and raises the error word.
+constexpr uint32_t kMaxPolls = 1u << 26;
+constexpr int kErrTimeout = 1;
+
+// Kernel shape shared by every scan kernel.
+constexpr int kThreads = 128;   // threads per CTA
+constexpr int kMaxSplits = 64;  // data-range splits per pass
+
+// Levels and bounds of Eq. 5 and Eq. 6, passed to kernels by value.
+struct AlphaMap {
+    double level[5];
+    double r_min, r_max;
+};
+
+struct DatasetDev {
+    const float2 *xy;     // [n_pad]
+    const float4 *xyzw;   // [n_pad] (x, y, z, 0)
+    const double2 *xy64;  // [n_pad]
+    const double *z64;    // [n_pad]
+    int64_t n;
+    int64_t n_pad;
+};
+
+// How one scan pass is cut into work: query blocks (one CTA each) times data-range splits,
+// each split a whole number of kPadPoints-point granules.
+struct PassPlan {
+    int q_per_block;   // queries handled by one CTA
+    int qblocks;       // ceil(m / q_per_block)
+    int splits;        // S: data-range splits, each scanned by its own CTA
+    int64_t split_len; // points per split (multiple of kPadPoints)
+};
+
+struct Plan {
+    int64_t m;
+    PassPlan knn;  // phase 1 scan
+    PassPlan w;    // phase 2 scan
+    bool with_idx; // keep neighbour indices (needed for the kNN output)
+};
+
+// Per-query parameters of phase 2 produced by the selection kernel.
+//   F32: w = ex2(fma(log2(d2), neg_s, c)), neg_s = -alpha/2, c = alpha/2 * log2(d1^2)
+//   F64: same with doubles.
+struct QParamF32 {
+    float neg_s;
+    float c;
+};
+struct QParamF64 {
+    double neg_s;
+    double c;
+};
+
+// Scratch buffers of one interpolation (device memory owned by the library or by the
+// caller of the allocation-free entry point).
+struct Scratch {
+    void *part_d2;     // [S_knn][k][m] float (F32) or double (F64): per-split sorted lists
+    int32_t *part_idx; // [S_knn][k][m] or null when indices are not kept
+    void *qparam;      // [m] QParamF32 / QParamF64
+    void *part_sum;    // [S_w][4][m] float (w_hi, w_lo, wz_hi, wz_lo) or double
+};
+
+size_t scratch_bytes(int precision, const Plan &pl, int k);
+void scratch_carve(void *base, int precision, const Plan &pl, int k, Scratch *s);
+
+// ---- launchers (all stream-ordered, return cudaGetLastError()) --------------------------
+cudaError_t launch_f32_knn(const DatasetDev &ds, const Plan &pl, const float *qx,
+                           const float *qy, int k, const Scratch &sc, int *err,
+                           cudaStream_t st);
+cudaError_t launch_f32_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
+                              const Scratch &sc, float *out_alpha, int32_t *out_knn,
+                              cudaStream_t st);
+cudaError_t launch_f32_weights(const DatasetDev &ds, const Plan &pl, const float *qx,
+                               const float *qy, const Scratch &sc, int *err, cudaStream_t st);
+cudaError_t launch_f32_finalize(const Plan &pl, const Scratch &sc, float *out,
+                                cudaStream_t st);
+
+cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *qx,
+                           const double *qy, int k, const Scratch &sc, int *err,
+                           cudaStream_t st);
+cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
+                              const Scratch &sc, float *out_alpha, int32_t *out_knn,
+                              cudaStream_t st);
+cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
+                               const double *qy, const Scratch &sc, int *err,
+                               cudaStream_t st);
+cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
+                                cudaStream_t st);
+
+// Shape of the kernels: queries per CTA of each scan and the CTA slots per SM that occupancy
+// allows (used to cut splits into whole waves).
+int f32_knn_queries_per_block(int k);
+int f32_w_queries_per_block();
+int f32_knn_slots_per_sm(int k, bool with_idx);
+int f32_w_slots_per_sm();
+int f64_knn_queries_per_block(int k);
+int f64_w_queries_per_block();
+int f64_knn_slots_per_sm(int k, bool with_idx);
+int f64_w_slots_per_sm();
+
+// Pipe-rate microbenchmarks (probe.cu).
+cudaError_t run_pipe_probe(int sm_count, aidw_pipe_rates *out);
+
+// ---- device helpers: Blackwell bulk-copy (TMA) and mbarrier ------------------------------
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared through the TMA unit; completion is signalled
+// on `bar` as transaction bytes. dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`. Returns false (and leaves the caller to raise
+// the error word) if the phase did not complete within kMaxPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t addr = smem_addr(bar);
+    for (uint32_t i = 0; i < kMaxPolls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// MUFU approximations with flush-to-zero (single SFU instruction each).
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Eq. 5 (Sec. 2.2 Step 2): fuzzy membership of the NN statistic, with pi / R_max as printed.
+__device__ __forceinline__ double membership_eq5(double R, const AlphaMap &am)
+{
+    if (R <= am.r_min)
+        return 0.0;
+    if (R >= am.r_max)
+        return 1.0;
+    return 0.5 - 0.5 * cos((3.141592653589793 / am.r_max) * (R - am.r_min));
+}
+
+// Eq. 6 (Sec. 2.2 Step 3): alpha is alpha_1 up to mu = 0.1, alpha_5 from mu = 0.9, and in
+// between runs linearly from alpha_s at mu = 0.1 + 0.2 (s - 1) to alpha_(s+1) 0.2 later.
+__device__ __forceinline__ double alpha_eq6(double mu, const AlphaMap &am)
+{
+    if (mu <= 0.1)
+        return am.level[0];
+    if (mu >= 0.9)
+        return am.level[4];
+    int seg = static_cast<int>((mu - 0.1) * 5.0);
+    seg = seg < 0 ? 0 : (seg > 3 ? 3 : seg);
+    const double t = (mu - (0.1 + 0.2 * seg)) * 5.0;
+    return am.level[seg] * (1.0 - t) + am.level[seg + 1] * t;
+}
+
+// Kahan step: adds v to the running sum h whose compensation (excess added so far) is c.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &h, T &c, T v)
+{
+    const T y = v - c;
+    const T t = h + y;
+    c = (t - h) - y;
+    h = t;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace aidw

@@ -1,0 +1,41 @@
+// Host-side runtime shared between the one-shot API (aidw_api.cu) and the batching / serving
+// layer (runtime.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "aidw_internal.cuh"
+
+struct aidw_ctx;
+
+namespace aidw {
+
+struct ServingRuntime;
+
+// Device memory from the context's pool, charged to its HBM budget (stream-ordered).
+int ctx_alloc(aidw_ctx *ctx, size_t bytes, cudaStream_t st, void **p);
+void ctx_free(aidw_ctx *ctx, void *p, size_t bytes, cudaStream_t st);
+size_t ctx_budget_left(aidw_ctx *ctx);
+int *ctx_err_word(aidw_ctx *ctx);
+int ctx_device(aidw_ctx *ctx);
+int ctx_sm_count(aidw_ctx *ctx);
+ServingRuntime *&ctx_serving(aidw_ctx *ctx);
+std::mutex &ctx_mutex(aidw_ctx *ctx);
+
+bool dataset_lookup(aidw_ctx *ctx, int64_t id, DatasetDev *dev, double *r_exp);
+int pointer_kind(const void *p, int device);
+int validate_params(const aidw_params *p, int64_t n);
+AlphaMap alpha_map(const aidw_params &p);
+Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bool with_idx,
+               int force_knn_splits, int force_w_splits);
+int interpolate_impl(aidw_ctx *ctx, int64_t dsid, const void *qx, const void *qy, int64_t m,
+                     const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
+                     cudaStream_t st, int force_knn_splits, int force_w_splits);
+int consume_device_error(aidw_ctx *ctx, cudaStream_t st);
+
+// Stops the serving thread (waits for admitted work) and frees its state; null is a no-op.
+void serving_stop(ServingRuntime *rt);
+
+}  // namespace aidw

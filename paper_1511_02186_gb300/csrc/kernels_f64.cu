@@ -1,0 +1,477 @@
+// FP64 kernels of the AIDW hot path for sm_103a: the same two scans as the FP32 path with
+// every step in double precision (Sec. 3.2.1 builds its kernels for float and double alike).
+// Squared distances of phase 1 are formed as dx*dx + dy*dy with each product and sum rounded
+// separately, so neighbour lists agree bit for bit with a reference that evaluates the same
+// expression in IEEE double without fused multiply-add. Ties go to the lower index.
+#include <math_constants.h>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+namespace {
+
+constexpr int kChunkKnn = 16;
+constexpr int kChunkW = 32;
+constexpr int kQW64 = 2;
+
+__device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
+{
+    const double dx = __dsub_rn(qx, px);
+    const double dy = __dsub_rn(qy, py);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ double dist2_eps(double qx, double qy, double px, double py)
+{
+    const double dx = __dsub_rn(qx, px);
+    const double dy = __dsub_rn(qy, py);
+    return __fma_rn(dx, dx, __fma_rn(dy, dy, kEpsF64));
+}
+
+template <int KP>
+__device__ __forceinline__ void list_insert(double (&L)[KP], double v)
+{
+    L[KP - 1] = v;
+#pragma unroll
+    for (int i = KP - 1; i > 0; --i) {
+        const double a = L[i - 1], b = L[i];
+        L[i - 1] = fmin(a, b);
+        L[i] = fmax(a, b);
+    }
+}
+
+template <int KP>
+__device__ __forceinline__ void index_insert(const double (&L)[KP], int32_t *base, double v,
+                                             int32_t id)
+{
+    int pos = 0;
+#pragma unroll
+    for (int i = 0; i < KP - 1; ++i)
+        pos += (L[i] <= v) ? 1 : 0;
+    for (int i = KP - 1; i > pos; --i)
+        base[i * kThreads] = base[(i - 1) * kThreads];
+    base[pos * kThreads] = id;
+}
+
+__device__ __forceinline__ void drain(uint64_t *bar, int t, int ntiles)
+{
+    for (int u = t; u < ntiles && u < t + 2; ++u)
+        (void)mbar_wait(&bar[u & 1], (u >> 1) & 1);
+}
+
+template <int KP, int Q, bool IDX>
+__global__ void __launch_bounds__(kThreads)
+f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
+               const double *__restrict__ qy, int k, double *__restrict__ part_d2,
+               int32_t *__restrict__ part_idx, int *__restrict__ err)
+{
+    __shared__ __align__(128) double2 tile[2][kTileF64Knn];
+    __shared__ __align__(8) uint64_t bar[2];
+    extern __shared__ int32_t idx_smem[];
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.y;
+    const int64_t qbase = static_cast<int64_t>(blockIdx.x) * pp.q_per_block;
+    const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
+    const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
+    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF64Knn);
+
+    double qxr[Q], qyr[Q];
+    double L[Q][KP];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        qxr[j] = qx[q];
+        qyr[j] = qy[q];
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+            L[j][i] = (i < KP - k) ? -CUDART_INF : CUDART_INF;
+        if (IDX) {
+#pragma unroll
+            for (int i = 0; i < KP; ++i)
+                idx_smem[(j * KP + i) * kThreads + tid] = -1;
+        }
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    constexpr uint32_t kBytes = kTileF64Knn * sizeof(double2);
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < ntiles; ++t) {
+            mbar_arrive_expect_tx(&bar[t], kBytes);
+            tma_load_1d(tile[t], ds.xy64 + p_begin + static_cast<int64_t>(t) * kTileF64Knn,
+                        kBytes, &bar[t]);
+        }
+    }
+    bool ok = true;
+    for (int t = 0; t < ntiles; ++t) {
+        const int b = t & 1;
+        const bool got = mbar_wait(&bar[b], (t >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            if (tid == 0) {
+                atomicOr(err, kErrTimeout);
+                drain(bar, t, ntiles);
+            }
+            break;
+        }
+        const int64_t pbase = p_begin + static_cast<int64_t>(t) * kTileF64Knn;
+        for (int c = 0; c < kTileF64Knn; c += kChunkKnn) {
+            double mn[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                mn[j] = CUDART_INF;
+#pragma unroll
+            for (int u = 0; u < kChunkKnn; ++u) {
+                const double2 p = tile[b][c + u];
+#pragma unroll
+                for (int j = 0; j < Q; ++j)
+                    mn[j] = fmin(mn[j], dist2_exact(qxr[j], qyr[j], p.x, p.y));
+            }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                any |= mn[j] < L[j][KP - 1];
+            if (any) {
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    if (mn[j] < L[j][KP - 1]) {
+#pragma unroll 1
+                        for (int u = 0; u < kChunkKnn; ++u) {
+                            const double2 p = tile[b][c + u];
+                            const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
+                            if (d < L[j][KP - 1]) {
+                                if (IDX)
+                                    index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
+                                                     d, static_cast<int32_t>(pbase + c + u));
+                                list_insert<KP>(L[j], d);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < ntiles) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[b], kBytes);
+            tma_load_1d(tile[b], ds.xy64 + pbase + 2 * kTileF64Knn, kBytes, &bar[b]);
+        }
+    }
+    if (!ok)
+        return;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = qbase + j * kThreads + tid;
+        if (q >= m)
+            continue;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            const int r = i - (KP - k);
+            if (r >= 0) {
+                const int64_t o = (static_cast<int64_t>(s) * k + r) * m + q;
+                part_d2[o] = L[j][i];
+                if (IDX)
+                    part_idx[o] = idx_smem[(j * KP + i) * kThreads + tid];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
+                  const double *__restrict__ part_d2, const int32_t *__restrict__ part_idx,
+                  QParamF64 *__restrict__ qp, float *__restrict__ out_alpha,
+                  int32_t *__restrict__ out_knn)
+{
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= m)
+        return;
+    int cur[kMaxSplits];
+    double hd[kMaxSplits];
+    int32_t hi[kMaxSplits];
+    for (int s = 0; s < S; ++s) {
+        cur[s] = 0;
+        const int64_t o = static_cast<int64_t>(s) * k * m + q;
+        hd[s] = part_d2[o];
+        hi[s] = part_idx ? part_idx[o] : 0;
+    }
+    double r_sum = 0.0, d1 = 0.0;
+    for (int r = 0; r < k; ++r) {
+        int bs = 0;
+        for (int s = 1; s < S; ++s)
+            if (hd[s] < hd[bs] || (hd[s] == hd[bs] && hi[s] < hi[bs]))
+                bs = s;
+        if (r == 0)
+            d1 = hd[bs];
+        r_sum = __dadd_rn(r_sum, __dsqrt_rn(hd[bs]));  // Eq. 3, ascending order
+        if (out_knn)
+            out_knn[q * k + r] = hi[bs];
+        if (++cur[bs] < k) {
+            const int64_t o = (static_cast<int64_t>(bs) * k + cur[bs]) * m + q;
+            hd[bs] = part_d2[o];
+            hi[bs] = part_idx ? part_idx[o] : 0;
+        } else {
+            hd[bs] = CUDART_INF;
+            hi[bs] = INT32_MAX;
+        }
+    }
+    const double r_obs = r_sum / k;
+    const double R = r_obs / r_exp;           // Eq. 4
+    const double mu = membership_eq5(R, am);  // Eq. 5
+    const double alpha = alpha_eq6(mu, am);   // Eq. 6
+    QParamF64 o;
+    if (d1 == 0.0) {
+        o.neg_s = -kCoincScaleF64;
+        o.c = kCoincScaleF64 * log2(kEpsF64);
+    } else {
+        const double sh = 0.5 * alpha;
+        o.neg_s = -sh;
+        o.c = sh * log2(__dadd_rn(d1, kEpsF64));
+    }
+    qp[q] = o;
+    if (out_alpha)
+        out_alpha[q] = static_cast<float>(alpha);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kThreads)
+f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
+                   const double *__restrict__ qy, const QParamF64 *__restrict__ qp,
+                   double *__restrict__ part_sum, int *__restrict__ err)
+{
+    __shared__ __align__(128) double2 txy[2][kTileF64W];
+    __shared__ __align__(128) double tz[2][kTileF64W];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.y;
+    const int64_t qbase = static_cast<int64_t>(blockIdx.x) * pp.q_per_block;
+    const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
+    const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
+    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF64W);
+
+    double qxr[Q], qyr[Q], ns[Q], cc[Q], hw[Q], cw[Q], hz[Q], cz[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        qxr[j] = qx[q];
+        qyr[j] = qy[q];
+        const QParamF64 o = qp[q];
+        ns[j] = o.neg_s;
+        cc[j] = o.c;
+        hw[j] = cw[j] = hz[j] = cz[j] = 0.0;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    constexpr uint32_t kBxy = kTileF64W * sizeof(double2);
+    constexpr uint32_t kBz = kTileF64W * sizeof(double);
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < ntiles; ++t) {
+            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileF64W;
+            mbar_arrive_expect_tx(&bar[t], kBxy + kBz);
+            tma_load_1d(txy[t], ds.xy64 + o, kBxy, &bar[t]);
+            tma_load_1d(tz[t], ds.z64 + o, kBz, &bar[t]);
+        }
+    }
+    bool ok = true;
+    for (int t = 0; t < ntiles; ++t) {
+        const int b = t & 1;
+        const bool got = mbar_wait(&bar[b], (t >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            if (tid == 0) {
+                atomicOr(err, kErrTimeout);
+                drain(bar, t, ntiles);
+            }
+            break;
+        }
+        for (int c = 0; c < kTileF64W; c += kChunkW) {
+            double sw[Q], sz[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                sw[j] = sz[j] = 0.0;
+#pragma unroll 4
+            for (int u = 0; u < kChunkW; ++u) {
+                const double2 p = txy[b][c + u];
+                const double pz = tz[b][c + u];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    const double d2 = dist2_eps(qxr[j], qyr[j], p.x, p.y);
+                    const double w = exp2(__fma_rn(log2(d2), ns[j], cc[j]));
+                    sw[j] = __dadd_rn(sw[j], w);
+                    sz[j] = __fma_rn(w, pz, sz[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                kahan_add(hw[j], cw[j], sw[j]);
+                kahan_add(hz[j], cz[j], sz[j]);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < ntiles) {
+            fence_proxy_async_smem();
+            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileF64W;
+            mbar_arrive_expect_tx(&bar[b], kBxy + kBz);
+            tma_load_1d(txy[b], ds.xy64 + o, kBxy, &bar[b]);
+            tma_load_1d(tz[b], ds.z64 + o, kBz, &bar[b]);
+        }
+    }
+    if (!ok)
+        return;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = qbase + j * kThreads + tid;
+        if (q >= m)
+            continue;
+        double *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
+        o[0] = hw[j];
+        o[m] = -cw[j];
+        o[2 * m] = hz[j];
+        o[3 * m] = -cz[j];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+f64_finalize_kernel(int64_t m, int S, const double *__restrict__ part_sum,
+                    double *__restrict__ out)
+{
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= m)
+        return;
+    double W = 0.0, Wc = 0.0, WZ = 0.0, WZc = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
+        kahan_add(W, Wc, o[0]);
+        kahan_add(W, Wc, o[m]);
+        kahan_add(WZ, WZc, o[2 * m]);
+        kahan_add(WZ, WZc, o[3 * m]);
+    }
+    out[q] = (WZ - WZc) / (W - Wc);  // Eq. 1
+}
+
+template <int KP>
+constexpr int knn_q64()
+{
+    return KP <= 16 ? 2 : 1;
+}
+
+template <int KP, bool IDX>
+cudaError_t launch_knn_t(const DatasetDev &ds, const Plan &pl, const double *qx,
+                         const double *qy, int k, const Scratch &sc, int *err, cudaStream_t st)
+{
+    constexpr int Q = knn_q64<KP>();
+    const size_t dyn = IDX ? sizeof(int32_t) * Q * KP * kThreads : 0;
+    auto fn = f64_knn_kernel<KP, Q, IDX>;
+    if (dyn > 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(dyn));
+        if (e != cudaSuccess)
+            return e;
+    }
+    dim3 grid(pl.knn.qblocks, pl.knn.splits);
+    fn<<<grid, kThreads, dyn, st>>>(ds, pl.m, pl.knn, qx, qy, k,
+                                    static_cast<double *>(sc.part_d2), sc.part_idx, err);
+    return cudaGetLastError();
+}
+
+template <int KP>
+int knn_slots_t(bool with_idx)
+{
+    constexpr int Q = knn_q64<KP>();
+    int n = 0;
+    if (with_idx) {
+        const size_t dyn = sizeof(int32_t) * Q * KP * kThreads;
+        cudaFuncSetAttribute(f64_knn_kernel<KP, Q, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_knn_kernel<KP, Q, true>, kThreads,
+                                                      dyn);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_knn_kernel<KP, Q, false>,
+                                                      kThreads, 0);
+    }
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+int f64_knn_queries_per_block(int k)
+{
+    return kThreads * (k <= 16 ? 2 : 1);
+}
+
+int f64_w_queries_per_block()
+{
+    return kThreads * kQW64;
+}
+
+int f64_knn_slots_per_sm(int k, bool with_idx)
+{
+    if (k <= 8)
+        return knn_slots_t<8>(with_idx);
+    if (k <= 16)
+        return knn_slots_t<16>(with_idx);
+    return knn_slots_t<32>(with_idx);
+}
+
+int f64_w_slots_per_sm()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_weights_kernel<kQW64>, kThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *qx,
+                           const double *qy, int k, const Scratch &sc, int *err,
+                           cudaStream_t st)
+{
+    if (k <= 8)
+        return pl.with_idx ? launch_knn_t<8, true>(ds, pl, qx, qy, k, sc, err, st)
+                           : launch_knn_t<8, false>(ds, pl, qx, qy, k, sc, err, st);
+    if (k <= 16)
+        return pl.with_idx ? launch_knn_t<16, true>(ds, pl, qx, qy, k, sc, err, st)
+                           : launch_knn_t<16, false>(ds, pl, qx, qy, k, sc, err, st);
+    return pl.with_idx ? launch_knn_t<32, true>(ds, pl, qx, qy, k, sc, err, st)
+                       : launch_knn_t<32, false>(ds, pl, qx, qy, k, sc, err, st);
+}
+
+cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
+                              const Scratch &sc, float *out_alpha, int32_t *out_knn,
+                              cudaStream_t st)
+{
+    const int64_t blocks = (pl.m + 255) / 256;
+    f64_select_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        pl.m, pl.knn.splits, k, r_exp, am, static_cast<const double *>(sc.part_d2),
+        pl.with_idx ? sc.part_idx : nullptr, static_cast<QParamF64 *>(sc.qparam), out_alpha,
+        out_knn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
+                               const double *qy, const Scratch &sc, int *err, cudaStream_t st)
+{
+    dim3 grid(pl.w.qblocks, pl.w.splits);
+    f64_weights_kernel<kQW64><<<grid, kThreads, 0, st>>>(
+        ds, pl.m, pl.w, qx, qy, static_cast<const QParamF64 *>(sc.qparam),
+        static_cast<double *>(sc.part_sum), err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
+                                cudaStream_t st)
+{
+    const int64_t blocks = (pl.m + 255) / 256;
+    f64_finalize_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        pl.m, pl.w.splits, static_cast<const double *>(sc.part_sum), out);
+    return cudaGetLastError();
+}
+
+}  // namespace aidw

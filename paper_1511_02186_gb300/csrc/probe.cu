@@ -1,0 +1,126 @@
+// Microbenchmarks of the pipes that bound the AIDW scans: FP32 FFMA, MUFU ex2 and lg2, and
+// FMNMX. Each kernel runs many independent dependency chains per thread on every SM and
+// records its own SM clock ticks and global-timer nanoseconds, so the result is in
+// instructions per clock per SM and the observed clock is reported beside it.
+#include <algorithm>
+#include <vector>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+constexpr int kProbeThreads = 512;
+
+struct ProbeTimes {
+    unsigned long long clk0, clk1, ns0, ns1;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seed, float *sink,
+                                                              ProbeTimes *times)
+{
+    float v[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        v[c] = seed + 0.001f * (threadIdx.x + c);
+    const float a = seed * 0.5f, b = 1.0f - seed;
+    __syncthreads();
+    const unsigned long long c0 = clock64(), n0 = global_ns();
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            if (OP == 0)
+                v[c] = __fmaf_rn(v[c], a, b);
+            else if (OP == 1)
+                v[c] = ex2_approx(v[c]);
+            else if (OP == 2)
+                v[c] = lg2_approx(v[c]);
+            else
+                v[c] = fminf(fmaxf(v[c], a), b);
+        }
+    }
+    __syncthreads();
+    const unsigned long long c1 = clock64(), n1 = global_ns();
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        s += v[c];
+    if (s == 12345.678f)
+        *sink = s;
+    if (threadIdx.x == 0)
+        times[blockIdx.x] = ProbeTimes{c0, c1, n0, n1};
+}
+
+template <int OP>
+cudaError_t run_one(int sm_count, int blocks_per_sm, float *sink, ProbeTimes *d_times,
+                    double *per_clk_sm, double *mhz)
+{
+    const int blocks = sm_count * blocks_per_sm;
+    probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);  // warm-up
+    probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return e;
+    std::vector<ProbeTimes> h(blocks);
+    e = cudaMemcpy(h.data(), d_times, sizeof(ProbeTimes) * blocks, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return e;
+    // Every block is resident at once (blocks_per_sm fits), so each SM's elapsed clocks is the
+    // longest block on it; take the median block duration as the per-SM span.
+    std::vector<double> clk(blocks), mh(blocks);
+    for (int i = 0; i < blocks; ++i) {
+        clk[i] = static_cast<double>(h[i].clk1 - h[i].clk0);
+        const double ns = static_cast<double>(h[i].ns1 - h[i].ns0);
+        mh[i] = ns > 0 ? clk[i] / ns * 1e3 : 0.0;
+    }
+    std::sort(clk.begin(), clk.end());
+    std::sort(mh.begin(), mh.end());
+    const double span = clk[blocks / 2];
+    const double ops_per_sm = static_cast<double>(blocks_per_sm) * kProbeThreads * kIters * kChains;
+    *per_clk_sm = ops_per_sm / span;
+    *mhz = mh[blocks / 2];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t run_pipe_probe(int sm_count, aidw_pipe_rates *out)
+{
+    float *sink = nullptr;
+    ProbeTimes *d_times = nullptr;
+    const int bps = 2;  // 2 x 512 threads: 32 warps per SM
+    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d_times, sizeof(ProbeTimes) * sm_count * bps);
+    double mhz[4] = {};
+    if (e == cudaSuccess)
+        e = run_one<0>(sm_count, bps, sink, d_times, &out->ffma_per_clk_sm, &mhz[0]);
+    if (e == cudaSuccess)
+        e = run_one<1>(sm_count, bps, sink, d_times, &out->ex2_per_clk_sm, &mhz[1]);
+    if (e == cudaSuccess)
+        e = run_one<2>(sm_count, bps, sink, d_times, &out->lg2_per_clk_sm, &mhz[2]);
+    if (e == cudaSuccess)
+        e = run_one<3>(sm_count, bps, sink, d_times, &out->fmnmx_per_clk_sm, &mhz[3]);
+    out->sm_clock_mhz = (mhz[0] + mhz[1] + mhz[2] + mhz[3]) / 4.0;
+    out->sm_count = sm_count;
+    out->reserved = 0;
+    // fmnmx probe runs two instructions (min and max) per chain step.
+    out->fmnmx_per_clk_sm *= 2.0;
+    if (sink)
+        cudaFree(sink);
+    if (d_times)
+        cudaFree(d_times);
+    return e;
+}
+
+}  // namespace aidw

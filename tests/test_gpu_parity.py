@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+FP32 path: Z within 1e-5 relative to max(|Z*|, S*), kNN sets equal up to FP32 distance ties.
+FP64 path: Z within 1e-12, kNN lists bit-identical (same order, ties to the lower index).
+"""
+import numpy as np
+import pytest
+
+from paper_1511_02186_gb300 import aidw, workloads
+from parity import TOL_F32, assert_parity, oracle_for, params_of, rel_err, run_gpu, to_device
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = [aidw.F32C, aidw.F64]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = aidw.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_uniform_unit_square_1024(ctx, precision):
+    """1,024 data x 1,024 queries uniform in the unit square, A = 1, k = 10."""
+    assert_parity(ctx, workloads.uniform_unit(0), precision)
+
+
+CASES = [
+    # (seed, n, m, k, pattern) -- several tiles, ragged tails, k around the list sizes
+    (1, 1, 1, 1, "uniform"),
+    (2, 7, 33, 7, "uniform"),
+    (3, 2047, 129, 10, "clustered"),
+    (4, 2049, 515, 8, "uniform"),
+    (5, 5000, 777, 9, "clustered"),
+    (6, 12345, 3001, 15, "clustered"),
+    (7, 4096, 1000, 16, "uniform"),
+    (8, 3000, 600, 17, "clustered"),
+    (9, 9000, 1500, 32, "clustered"),
+    (10, 33, 257, 33 - 1, "uniform"),
+]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"n{c[1]}m{c[2]}k{c[3]}{c[4][0]}")
+def test_small_cases(ctx, precision, case):
+    seed, n, m, k, pat = case
+    wl = workloads.small_case(seed, n, m, k=k, pattern=pat)
+    assert_parity(ctx, wl, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("splits", [(2, 3), (5, 7), (7, 1), (1, 6)])
+def test_forced_splits_merge(ctx, precision, splits):
+    """Data-range splits restart the neighbour lists and partial sums; merges must agree."""
+    wl = workloads.small_case(21, 14000, 900, k=12, pattern="clustered")
+    assert_parity(ctx, wl, precision, splits=splits)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_alpha_covers_every_level(ctx, precision):
+    """Clustered data with k = 10 spans R from clustered to dispersed (all Eq. 6 segments),
+    with non-monotone levels and R_min > 0 (Eq. 5 read with pi / R_max)."""
+    wl = workloads.small_case(31, 20000, 2000, k=10, pattern="clustered",
+                              levels=(0.7, 2.5, 1.2, 4.0, 3.1))
+    wl.r_min, wl.r_max = 0.2, 2.2
+    assert_parity(ctx, wl, precision)
+    ref, _ = oracle_for(wl, precision)
+    segs = np.digitize(ref["alpha"], [0.7 + 1e-9])
+    assert len(np.unique(np.round(ref["alpha"], 6))) > 50, "alpha should spread over levels"
+    del segs
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_equal_levels_is_standard_idw(ctx, precision):
+    wl = workloads.small_case(41, 3000, 400, k=5, pattern="clustered", levels=(2.0,) * 5)
+    assert_parity(ctx, wl, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_coincident_and_duplicate_points(ctx, precision):
+    """Queries on data points, duplicated data points and collinear ties."""
+    wl = workloads.small_case(51, 500, 200, k=6, pattern="uniform")
+    x, y, z = wl.x.copy(), wl.y.copy(), wl.z.copy()
+    x[10:20], y[10:20] = x[0], y[0]          # ten duplicates of point 0
+    x[100], y[100] = x[99], y[99]
+    wl.x, wl.y = x, y
+    qx, qy = wl.qx.copy(), wl.qy.copy()
+    qx[:5], qy[:5] = x[[0, 99, 300, 301, 499]], y[[0, 99, 300, 301, 499]]
+    wl.qx, wl.qy = qx, qy
+    z_gpu, a, kn = run_gpu(ctx, wl, precision)
+    assert_parity(ctx, wl, precision, gpu=(z_gpu, a, kn))
+    src = wl.as_f32() if precision == aidw.F32C else wl
+    expect0 = np.mean(np.concatenate([[src.z[0]], src.z[10:20]]))
+    assert abs(z_gpu[0] - expect0) <= 1e-6 * max(1, abs(expect0))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_lattice_ties(ctx, precision):
+    """Integer lattice data: many exactly equal distances; kNN ties go to the lower index."""
+    rng = np.random.default_rng(61)
+    g = np.arange(40, dtype=float)
+    gx, gy = np.meshgrid(g, g)
+    perm = rng.permutation(1600)
+    wl = workloads.Workload("lattice", gx.ravel()[perm], gy.ravel()[perm],
+                            rng.standard_normal(1600), 1600.0,
+                            rng.integers(0, 80, 300) / 2.0, rng.integers(0, 80, 300) / 2.0, k=9)
+    assert_parity(ctx, wl, precision)
+
+
+def test_host_arrays_match_device_arrays(ctx):
+    wl = workloads.small_case(71, 6000, 1234, k=10, pattern="clustered")
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    p = params_of(wl, aidw.F32C)
+    zh, ah, kh = ctx.interpolate(ds, wl.qx.astype(np.float32), wl.qy.astype(np.float32), p,
+                                 want_alpha=True, want_knn=True)
+    zd, ad, kd = run_gpu(ctx, wl, aidw.F32C, ds=ds)
+    assert np.array_equal(zh.astype(np.float64), zd)
+    assert np.array_equal(kh, kd)
+    ds.destroy()
+
+
+def test_deterministic(ctx):
+    wl = workloads.small_case(81, 30000, 5000, k=10, pattern="clustered")
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    a = run_gpu(ctx, wl, aidw.F32C, ds=ds)
+    b = run_gpu(ctx, wl, aidw.F32C, ds=ds)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    ds.destroy()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_standard_idw_entry_point(ctx, precision):
+    import oracle
+    import torch
+    wl = workloads.small_case(91, 7000, 800, pattern="clustered")
+    src = wl.as_f32() if precision == aidw.F32C else wl
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, precision)
+    for p in (1.0, 2.0, 3.5):
+        out = ctx.idw(ds, qx, qy, p, precision)
+        torch.cuda.synchronize()
+        ref = oracle.idw(src.x, src.y, src.z, src.qx, src.qy, p)
+        err = rel_err(out.cpu().numpy(), ref)
+        assert err.max() <= (TOL_F32 if precision == aidw.F32C else 1e-12)
+    ds.destroy()
+
+
+def test_paper_scale_uniform_sampled(ctx):
+    """1,048,576 x 1,048,576 uniform in [0,1000]^2 at the benchmark's launch configuration;
+    4,096 sampled queries against the oracle, every output checked for its invariants."""
+    wl = workloads.uniform_paper(0)
+    z, a, kn = run_gpu(ctx, wl, aidw.F32C, want_knn=False)
+    assert np.all(np.isfinite(z))
+    zf = wl.as_f32().z
+    assert z.min() >= zf.min() - 1e-5 and z.max() <= zf.max() + 1e-5
+    assert a.min() >= 1.0 - 1e-6 and a.max() <= 5.0 + 1e-6
+    idx = np.random.default_rng(5).choice(wl.m, 4096, replace=False)
+    ref, _ = oracle_for(wl, aidw.F32C, idx)
+    err = rel_err(z[idx], ref)
+    assert err.max() <= TOL_F32, err.max()
+    assert np.abs(a[idx] - ref["alpha"]).max() <= 1e-5
+
+
+def test_clustered_grid_sampled(ctx):
+    """2,097,152 clustered data points x 1448^2 grid queries, z lognormal: alpha spans every
+    level; 2,048 sampled queries (half random, half the most clustered) against the oracle."""
+    wl = workloads.clustered_grid(0)
+    z, a, _ = run_gpu(ctx, wl, aidw.F32C, want_knn=False)
+    assert np.all(np.isfinite(z)) and np.all(z > 0)
+    rng = np.random.default_rng(6)
+    idx = np.unique(np.concatenate([rng.choice(wl.m, 1024, replace=False),
+                                    np.argsort(a)[:1024]]))
+    ref, _ = oracle_for(wl, aidw.F32C, idx)
+    err = np.abs(z[idx] - ref["z"]) / np.abs(ref["z"])   # z > 0: pure relative error
+    assert err.max() <= TOL_F32, err.max()
+    assert ref["alpha"].min() < 1.5 and ref["alpha"].max() > 4.5
+
+
+def test_fp64_paper_scale_sampled_queries(ctx):
+    """FP64 path on the full 1,048,576-point dataset for 4,096 queries: Z within 1e-12 and
+    kNN lists bit-identical."""
+    wl = workloads.uniform_paper(0)
+    idx = np.random.default_rng(7).choice(wl.m, 4096, replace=False)
+    sub = wl.query_subset(idx)
+    assert_parity(ctx, sub, aidw.F64)
+
+
+# ---- argument and failure handling on the device ---------------------------------------------
+
+def test_invalid_arguments(ctx):
+    wl = workloads.small_case(101, 100, 10)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F32C)
+    for bad in (dict(k=0), dict(k=101), dict(k=33), dict(levels=(1, 2, float("nan"), 4, 5)),
+                dict(r_min=2.0, r_max=1.0), dict(levels=(1, 2, -3, 4, 5))):
+        kw = dict(k=5)
+        kw.update(bad)
+        with pytest.raises(aidw.AidwError) as e:
+            ctx.interpolate(ds, qx, qy, aidw.default_params(**kw))
+        assert e.value.status == aidw.ERR_INVALID_ARG
+    bad_q = wl.qx.astype(np.float32)
+    bad_q[3] = np.inf
+    with pytest.raises(aidw.AidwError):
+        ctx.interpolate(ds, bad_q, wl.qy.astype(np.float32), aidw.default_params(k=5))
+    ds.destroy()
+    with pytest.raises(aidw.AidwError) as e:
+        ctx.interpolate(ds, qx, qy, aidw.default_params(k=5))
+    assert e.value.status == aidw.ERR_INVALID_ARG or e.value.status == aidw.ERR_NOT_FOUND
+    x = wl.x.copy()
+    x[7] = np.nan
+    with pytest.raises(aidw.AidwError) as e:
+        ctx.create_dataset(x, wl.y, wl.z, wl.area)
+    assert e.value.status == aidw.ERR_INVALID_ARG
+    with pytest.raises(aidw.AidwError):
+        ctx.create_dataset(wl.x, wl.y, wl.z, 0.0)
+
+
+def test_budget_and_injected_allocation_failure(ctx):
+    wl = workloads.small_case(111, 5000, 500)
+    small = aidw.Context(0, hbm_budget=1 << 20)
+    with pytest.raises(aidw.AidwError) as e:
+        small.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    assert e.value.status == aidw.ERR_OOM
+    small.close()
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    ctx.fail_alloc_after(0)
+    qx, qy = to_device(wl, aidw.F32C)
+    with pytest.raises(aidw.AidwError) as e:
+        ctx.interpolate(ds, qx, qy, aidw.default_params())
+    assert e.value.status == aidw.ERR_OOM
+    out, _, _ = ctx.interpolate(ds, qx, qy, aidw.default_params())  # recovers
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    ds.destroy()
