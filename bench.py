@@ -40,7 +40,9 @@ LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per 
 
 
 def workload_config(wl):
-    return {"workload": "uniform_paper_1M_x_1M", "n_data": wl.n, "m_query": wl.m, "k": wl.k,
+    name = "uniform_paper_1M_x_1M" if wl.n == N_DATA and wl.m == M_QUERY else \
+        f"uniform_paper_{wl.n}_x_{wl.m}"
+    return {"workload": name, "n_data": wl.n, "m_query": wl.m, "k": wl.k,
             "levels": list(wl.levels), "r_min": wl.r_min, "r_max": wl.r_max, "area": wl.area,
             "domain": "[0,1000]^2", "seed": 0,
             "l2": "flushed between timed steps by a 256 MiB write (outside the timed events)"}
@@ -206,7 +208,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     __graft_entry__.build()
-    wl = workloads.uniform_paper(0)
+    wl = workloads.uniform_paper(0, n=args.n, m=args.n)
     ctx = aidw.Context(local)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
     qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)
@@ -280,6 +282,18 @@ def run_gpu(args):
         peak = peak_pairs(FP32_OPS_P1, 0)
     step_peak = peak_pairs(FP32_OPS_P1 + FP32_OPS_P2, MUFU_OPS_P2)
     kernel_sum_s = (kn + kw + ks + kf) / 1e3
+
+    if not args.extras:
+        ds.destroy()
+        ctx.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "config": workload_config(wl),
+                              "kernel_ms": {"knn": kn, "select": ks, "weights": kw,
+                                            "finalize": kf},
+                              "note": "profiling run without the extra measurements"}))
+        return 0
 
     # FP64 path on a query sample of the same dataset (same per-query work).
     q64 = 8192
@@ -373,6 +387,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=N_DATA,
+                    help="data and query count (smaller sizes only for profiling runs)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the FP64, end-to-end and CPU-baseline measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

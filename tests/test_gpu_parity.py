@@ -221,7 +221,7 @@ def test_invalid_arguments(ctx):
 
 def test_budget_and_injected_allocation_failure(ctx):
     wl = workloads.small_case(111, 5000, 500)
-    small = aidw.Context(0, hbm_budget=1 << 20)
+    small = aidw.Context(0, hbm_budget=64 << 10)
     with pytest.raises(aidw.AidwError) as e:
         small.create_dataset(wl.x, wl.y, wl.z, wl.area)
     assert e.value.status == aidw.ERR_OOM
