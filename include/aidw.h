@@ -126,6 +126,25 @@ int aidw_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void 
 int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
              double alpha, int32_t precision, void *out, void *stream);
 
+/* Allocation-free variant of aidw_interpolate for AIDW_F32C (the paper has no counterpart:
+ * it concerns how this library obtains memory, not the method). For callers that must not
+ * allocate device memory while serving a call, e.g. a process whose device footprint is fixed
+ * at start-up and may not grow or fail mid-request, or code that cannot accept the implicit
+ * device synchronisation of cudaFree: this call performs no cudaMalloc, cudaFree or other
+ * allocation. Its scratch is one 16 MiB __device__ array inside the library, held on every
+ * GPU that loads the library until the process exits. The context and the dataset are
+ * created beforehand (they allocate once, at set-up).
+ *   qx, qy, out  DEVICE arrays of m floats on the context's device (host arrays are rejected)
+ *   p            as for aidw_interpolate; p->precision must be AIDW_F32C
+ * Limit: about m * (4k + 24) bytes must fit in 16 MiB (m <= 262,144 for k = 10, about
+ * 110,000 for k = 32); larger calls return AIDW_ERR_INVALID_ARG. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that first call before
+ * any stream capture. All calls share the one array: calls whose work overlaps on the GPU (for example
+ * on two streams) race and must be serialised by the caller. Stream-ordered on `stream`;
+ * kernel timeouts are reported by aidw_check_device_errors. */
+int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, const float *qy,
+                             int64_t m, const aidw_params *p, float *out, void *stream);
+
 /* ---- batched launch (many datasets in one persistent kernel) -------------------------- */
 /* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays) and params.
  * All entries of one batch share the precision AIDW_F32C. */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "aidw_dataset_info": (ctypes.c_int, [_P, _I64, _P, _P]),
     "aidw_interpolate": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "aidw_idw": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _D, _I32, _P, _P]),
+    "aidw_interpolate_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P]),
     "aidw_interpolate_batch": (ctypes.c_int, [_P, _P, _I32, _P]),
     "aidw_submit": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "aidw_poll": (ctypes.c_int, [_P, _I64, _P]),

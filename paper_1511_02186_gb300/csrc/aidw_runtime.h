@@ -34,6 +34,10 @@ int interpolate_impl(aidw_ctx *ctx, int64_t dsid, const void *qx, const void *qy
                      const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
                      cudaStream_t st, int force_knn_splits, int force_w_splits);
 int consume_device_error(aidw_ctx *ctx, cudaStream_t st);
+int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
+                          const aidw_params &p, const void *qx, const void *qy,
+                          const Scratch &sc, void *out, float *out_alpha, int32_t *out_knn,
+                          cudaStream_t st, bool profile);
 
 // Stops the serving thread (waits for admitted work) and frees its state; null is a no-op.
 void serving_stop(ServingRuntime *rt);
