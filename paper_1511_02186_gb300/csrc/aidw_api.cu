@@ -27,7 +27,7 @@ inline size_t align256(size_t b)
 template <typename T>
 __global__ void convert_dataset_kernel(const T *__restrict__ x, const T *__restrict__ y,
                                        const T *__restrict__ z, int64_t n, int64_t n_pad,
-                                       float2 *xy, float4 *xyzw, double2 *xy64, double *z64,
+                                       float4 *nxy2, float2 *zz, double2 *xy64, double *z64,
                                        unsigned long long *bad)
 {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -49,8 +49,8 @@ __global__ void convert_dataset_kernel(const T *__restrict__ x, const T *__restr
         // FP32 copies must stay finite too (coordinates beyond float range are rejected).
         if (i < n && !(isfinite(fa) && isfinite(fb) && isfinite(fc)))
             ++nb;
-        xy[i] = make_float2(fa, fb);
-        xyzw[i] = make_float4(fa, fb, fc, 0.0f);
+        nxy2[i] = make_float4(-fa, -fa, -fb, -fb);
+        zz[i] = make_float2(fc, fc);
         xy64[i] = make_double2(a, b);
         z64[i] = c;
     }
@@ -88,7 +88,7 @@ struct aidw_ctx {
     cudaEvent_t ev[5] = {};
     aidw_kernel_times last{};
     bool last_valid = false;
-    int slots_cache[2][3][2] = {};  // [precision][kp bucket][with_idx] knn slots
+    int slots_cache[2][4][2] = {};  // [precision][kp bucket][with_idx] knn slots
     int wslots_cache[2] = {};
     ServingRuntime *serving = nullptr;
 };
@@ -220,7 +220,7 @@ static PassPlan plan_pass(int64_t m, int64_t n_pad, int qpb, int slots_total, in
 
 static int kp_bucket(int k)
 {
-    return k <= 8 ? 0 : (k <= 16 ? 1 : 2);
+    return k <= 8 ? 0 : (k <= 12 ? 1 : (k <= 16 ? 2 : 3));
 }
 
 Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bool with_idx,
@@ -239,9 +239,10 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     const int qk = precision == AIDW_F64 ? f64_knn_queries_per_block(k)
                                          : f32_knn_queries_per_block(k);
     const int qw = precision == AIDW_F64 ? f64_w_queries_per_block() : f32_w_queries_per_block();
-    // A split restarts its neighbour lists, costing about k log(n/k) insertions per query;
-    // it is charged as a few thousand points of scan.
-    pl.knn = plan_pass(m, n_pad, qk, ks * ctx->sm_count, 4096 + 256 * k);
+    // A split restarts its neighbour lists: about k (1 + ln(n_split / k)) insertions per query,
+    // each a rescan of a chunk by a partly idle warp. Measured on GB300 at n = m = 2^20,
+    // k = 10, every extra split costs about as much as scanning 100,000 more points.
+    pl.knn = plan_pass(m, n_pad, qk, ks * ctx->sm_count, 10000 * k);
     pl.w = plan_pass(m, n_pad, qw, ws * ctx->sm_count, 1024);
     const int64_t G = n_pad / kPadPoints;
     auto force = [&](PassPlan &pp, int S) {
@@ -621,7 +622,7 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     const size_t es = dtype == AIDW_DTYPE_F64 ? sizeof(double) : sizeof(float);
     const int64_t n_pad = (n + kPadPoints - 1) / kPadPoints * kPadPoints;
     const size_t np = static_cast<size_t>(n_pad);
-    const size_t bytes = align256(np * sizeof(float2)) + align256(np * sizeof(float4)) +
+    const size_t bytes = align256(np * sizeof(float4)) + align256(np * sizeof(float2)) +
                          align256(np * sizeof(double2)) + align256(np * sizeof(double));
     {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -674,10 +675,10 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     }
     DatasetRec rec;
     char *b = static_cast<char *>(blk);
-    float2 *xy = reinterpret_cast<float2 *>(b);
-    b += align256(np * sizeof(float2));
-    float4 *xyzw = reinterpret_cast<float4 *>(b);
+    float4 *nxy2 = reinterpret_cast<float4 *>(b);
     b += align256(np * sizeof(float4));
+    float2 *zz = reinterpret_cast<float2 *>(b);
+    b += align256(np * sizeof(float2));
     double2 *xy64 = reinterpret_cast<double2 *>(b);
     b += align256(np * sizeof(double2));
     double *z64 = reinterpret_cast<double *>(b);
@@ -688,11 +689,11 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     if (dtype == AIDW_DTYPE_F64)
         convert_dataset_kernel<double><<<blocks, threads>>>(
             static_cast<const double *>(sx), static_cast<const double *>(sy),
-            static_cast<const double *>(sz), n, n_pad, xy, xyzw, xy64, z64, ctx->d_bad);
+            static_cast<const double *>(sz), n, n_pad, nxy2, zz, xy64, z64, ctx->d_bad);
     else
         convert_dataset_kernel<float><<<blocks, threads>>>(
             static_cast<const float *>(sx), static_cast<const float *>(sy),
-            static_cast<const float *>(sz), n, n_pad, xy, xyzw, xy64, z64, ctx->d_bad);
+            static_cast<const float *>(sz), n, n_pad, nxy2, zz, xy64, z64, ctx->d_bad);
     unsigned long long bad = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpy(&bad, ctx->d_bad, sizeof(bad), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -706,8 +707,8 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
         unreserve();
         return rc;
     }
-    rec.dev.xy = xy;
-    rec.dev.xyzw = xyzw;
+    rec.dev.nxy2 = nxy2;
+    rec.dev.zz = zz;
     rec.dev.xy64 = xy64;
     rec.dev.z64 = z64;
     rec.dev.n = n;

@@ -12,8 +12,8 @@ namespace aidw {
 // Data points per shared-memory tile. Dataset arrays are padded to a multiple of
 // kPadPoints with sentinel points at +infinity (value 0), which never enter a neighbour list
 // and get weight 0, so every tile is full and every TMA copy has a whole-tile size.
-constexpr int kTileF32Knn = 1024;  // float2 (x, y): 8 KiB per buffer
-constexpr int kTileF32W = 512;     // float4 (x, y, z, 0): 8 KiB per buffer
+constexpr int kTileF32Knn = 512;   // float4 (-x, -x, -y, -y): 8 KiB per buffer
+constexpr int kTileF32W = 512;     // float4 (-x, -x, -y, -y) + float2 (z, z): 12 KiB per buffer
 constexpr int kTileF64Knn = 512;   // double2 (x, y): 8 KiB per buffer
 constexpr int kTileF64W = 512;     // double2 + double: 12 KiB per buffer
 constexpr int kPadPoints = 2048;   // common multiple of every tile and split granule
@@ -42,9 +42,12 @@ struct AlphaMap {
     double r_min, r_max;
 };
 
+// FP32 copies are stored negated and duplicated, (-x, -x, -y, -y) and (z, z), so that one
+// shared-memory load yields the register pairs that packed FP32x2 instructions operate on for
+// two queries at once (q + (-x) is exactly q - x).
 struct DatasetDev {
-    const float2 *xy;     // [n_pad]
-    const float4 *xyzw;   // [n_pad] (x, y, z, 0)
+    const float4 *nxy2;   // [n_pad] (-x, -x, -y, -y)
+    const float2 *zz;     // [n_pad] (z, z)
     const double2 *xy64;  // [n_pad]
     const double *z64;    // [n_pad]
     int64_t n;

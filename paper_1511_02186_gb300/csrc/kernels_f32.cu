@@ -20,13 +20,14 @@
 namespace aidw {
 namespace {
 
-constexpr int kChunkKnn = 16;  // points between neighbour-list threshold checks
+constexpr int kChunkKnn = 8;   // points between neighbour-list threshold checks
 constexpr int kChunkW = 32;    // points summed in plain FP32 before a Kahan merge
 
-__device__ __forceinline__ float dist2_f32(float qx, float qy, float px, float py)
+// Squared distance from negated data coordinates: q + (-p) is exactly q - p.
+__device__ __forceinline__ float dist2_neg(float qx, float qy, float npx, float npy)
 {
-    const float dx = __fsub_rn(qx, px);
-    const float dy = __fsub_rn(qy, py);
+    const float dx = __fadd_rn(qx, npx);
+    const float dy = __fadd_rn(qy, npy);
     return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, kEpsF32));
 }
 
@@ -59,11 +60,6 @@ __device__ __forceinline__ void index_insert(const float (&L)[KP], int32_t *base
     base[pos * kThreads] = id;
 }
 
-struct PipeState {
-    uint64_t *bar;
-    bool ok;
-};
-
 // Bounded wait for both buffers' outstanding copies after an abandoned scan.
 __device__ __forceinline__ void drain(uint64_t *bar, int t, int ntiles)
 {
@@ -73,14 +69,37 @@ __device__ __forceinline__ void drain(uint64_t *bar, int t, int ntiles)
 
 // ---------------------------------------------------------------------------------------------
 // Phase 1: per (query block, split) neighbour lists.
+//
+// Each thread owns Q queries, processed as Q/2 packed pairs. For every data point and pair the
+// hot loop evaluates, with FP32x2 instructions, v = dx^2 + (dy^2 - T') where T' is the k-th
+// squared distance enlarged by 2^-20 (relative); the sign bits of v are OR-ed per query over a
+// 16-point chunk. A negative v is necessary for a point to enter the list: if the exact FP32
+// distance d2 = fl(dx^2 + fl(dy^2)) is below T then the real dx^2 + dy^2 is below T(1 + 2^-23)
+// and v, computed with at most u T' of error, stays below zero. Only for a query whose sign bit
+// is set the chunk is rescanned with the exact distance, which alone decides insertion, so the
+// neighbour lists are exactly those of the plain scan.
 // ---------------------------------------------------------------------------------------------
+constexpr float kFilterMargin = 1.0f + 9.5367431640625e-07f;  // 1 + 2^-20
+
+__device__ __forceinline__ float neg_filter_threshold(float kth)
+{
+    return -(kth * kFilterMargin);
+}
+
+__device__ __forceinline__ uint32_t sign_or3(uint32_t acc, float a, float b)
+{
+    return acc | __float_as_uint(a) | __float_as_uint(b);
+}
+
 template <int KP, int Q, bool IDX>
 __global__ void __launch_bounds__(kThreads)
 f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ qx,
                const float *__restrict__ qy, int k, float *__restrict__ part_d2,
                int32_t *__restrict__ part_idx, int *__restrict__ err)
 {
-    __shared__ __align__(128) float2 tile[2][kTileF32Knn];
+    static_assert(Q % 2 == 0, "queries are processed in packed pairs");
+    constexpr int H = Q / 2;
+    __shared__ __align__(128) float4 tile[2][kTileF32Knn];
     __shared__ __align__(8) uint64_t bar[2];
     extern __shared__ int32_t idx_smem[];  // [Q][KP][kThreads] when IDX
 
@@ -91,13 +110,19 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
     const int ntiles = static_cast<int>((p_end - p_begin) / kTileF32Knn);
 
-    float qxr[Q], qyr[Q];
+    float2 qxp[H], qyp[H], nthr[H];
     float L[Q][KP];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int64_t q = min(qbase + j * kThreads + tid, m - 1);
-        qxr[j] = qx[q];
-        qyr[j] = qy[q];
+        const float a = qx[q], b = qy[q];
+        if (j & 1) {
+            qxp[j / 2].y = a;
+            qyp[j / 2].y = b;
+        } else {
+            qxp[j / 2].x = a;
+            qyp[j / 2].x = b;
+        }
 #pragma unroll
         for (int i = 0; i < KP; ++i)
             L[j][i] = (i < KP - k) ? -CUDART_INF_F : CUDART_INF_F;
@@ -107,6 +132,9 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
                 idx_smem[(j * KP + i) * kThreads + tid] = -1;
         }
     }
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        nthr[h] = make_float2(-CUDART_INF_F, -CUDART_INF_F);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -114,11 +142,11 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
         fence_mbar_init();
     }
     __syncthreads();
-    constexpr uint32_t kBytes = kTileF32Knn * sizeof(float2);
+    constexpr uint32_t kBytes = kTileF32Knn * sizeof(float4);
     if (tid == 0) {
         for (int t = 0; t < 2 && t < ntiles; ++t) {
             mbar_arrive_expect_tx(&bar[t], kBytes);
-            tma_load_1d(tile[t], ds.xy + p_begin + static_cast<int64_t>(t) * kTileF32Knn,
+            tma_load_1d(tile[t], ds.nxy2 + p_begin + static_cast<int64_t>(t) * kTileF32Knn,
                         kBytes, &bar[t]);
         }
     }
@@ -135,34 +163,43 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
             }
             break;
         }
-        const float4 *t4 = reinterpret_cast<const float4 *>(tile[b]);
+        const float4 *tb = tile[b];
         const int64_t pbase = p_begin + static_cast<int64_t>(t) * kTileF32Knn;
         for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
-            float mn[Q];
+            uint32_t acc[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                mn[j] = CUDART_INF_F;
+                acc[j] = 0u;
 #pragma unroll
-            for (int u = 0; u < kChunkKnn / 2; ++u) {
-                const float4 p = t4[c / 2 + u];
+            for (int u = 0; u < kChunkKnn; u += 2) {
+                const float4 pa = tb[c + u];
+                const float4 pb = tb[c + u + 1];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    mn[j] = fminf(mn[j], dist2_f32(qxr[j], qyr[j], p.x, p.y));
-                    mn[j] = fminf(mn[j], dist2_f32(qxr[j], qyr[j], p.z, p.w));
+                for (int h = 0; h < H; ++h) {
+                    const float2 dxa = __fadd2_rn(qxp[h], make_float2(pa.x, pa.y));
+                    const float2 dya = __fadd2_rn(qyp[h], make_float2(pa.z, pa.w));
+                    const float2 va = __ffma2_rn(dxa, dxa, __ffma2_rn(dya, dya, nthr[h]));
+                    const float2 dxb = __fadd2_rn(qxp[h], make_float2(pb.x, pb.y));
+                    const float2 dyb = __fadd2_rn(qyp[h], make_float2(pb.z, pb.w));
+                    const float2 vb = __ffma2_rn(dxb, dxb, __ffma2_rn(dyb, dyb, nthr[h]));
+                    acc[2 * h] = sign_or3(acc[2 * h], va.x, vb.x);
+                    acc[2 * h + 1] = sign_or3(acc[2 * h + 1], va.y, vb.y);
                 }
             }
-            bool any = false;
+            uint32_t any = 0u;
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                any |= mn[j] < L[j][KP - 1];
-            if (any) {
+                any |= acc[j];
+            if (static_cast<int32_t>(any) < 0) {
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
-                    if (mn[j] < L[j][KP - 1]) {
+                    if (static_cast<int32_t>(acc[j]) < 0) {
+                        const float qxj = (j & 1) ? qxp[j / 2].y : qxp[j / 2].x;
+                        const float qyj = (j & 1) ? qyp[j / 2].y : qyp[j / 2].x;
 #pragma unroll 1
                         for (int u = 0; u < kChunkKnn; ++u) {
-                            const float2 p = tile[b][c + u];
-                            const float d = dist2_f32(qxr[j], qyr[j], p.x, p.y);
+                            const float4 p = tb[c + u];
+                            const float d = dist2_neg(qxj, qyj, p.x, p.z);
                             if (d < L[j][KP - 1]) {
                                 if (IDX)
                                     index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
@@ -170,6 +207,11 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
                                 list_insert<KP>(L[j], d);
                             }
                         }
+                        const float nt = neg_filter_threshold(L[j][KP - 1]);
+                        if (j & 1)
+                            nthr[j / 2].y = nt;
+                        else
+                            nthr[j / 2].x = nt;
                     }
                 }
             }
@@ -178,7 +220,7 @@ f32_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ 
         if (tid == 0 && t + 2 < ntiles) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[b], kBytes);
-            tma_load_1d(tile[b], ds.xy + pbase + 2 * kTileF32Knn, kBytes, &bar[b]);
+            tma_load_1d(tile[b], ds.nxy2 + pbase + 2 * kTileF32Knn, kBytes, &bar[b]);
         }
     }
     if (!ok)
@@ -271,7 +313,8 @@ f32_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phase 2: per (query block, split) weighted sums.
+// Phase 2: per (query block, split) weighted sums. Q queries per thread in packed pairs: the
+// distance, power scale and both sums run as FP32x2 instructions, lg2 and ex2 on the MUFU.
 // ---------------------------------------------------------------------------------------------
 template <int Q>
 __global__ void __launch_bounds__(kThreads)
@@ -279,7 +322,10 @@ f32_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restric
                    const float *__restrict__ qy, const QParamF32 *__restrict__ qp,
                    float *__restrict__ part_sum, int *__restrict__ err)
 {
-    __shared__ __align__(128) float4 tile[2][kTileF32W];
+    static_assert(Q % 2 == 0, "queries are processed in packed pairs");
+    constexpr int H = Q / 2;
+    __shared__ __align__(128) float4 txy[2][kTileF32W];
+    __shared__ __align__(128) float2 tz[2][kTileF32W];
     __shared__ __align__(8) uint64_t bar[2];
 
     const int tid = threadIdx.x;
@@ -289,18 +335,27 @@ f32_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restric
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
     const int ntiles = static_cast<int>((p_end - p_begin) / kTileF32W);
 
-    float qxr[Q], qyr[Q], ns[Q], cc[Q];
+    float2 qxp[H], qyp[H], nsp[H], ccp[H];
     float hw[Q], cw[Q], hz[Q], cz[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int64_t q = min(qbase + j * kThreads + tid, m - 1);
-        qxr[j] = qx[q];
-        qyr[j] = qy[q];
         const QParamF32 o = qp[q];
-        ns[j] = o.neg_s;
-        cc[j] = o.c;
+        const float a = qx[q], b = qy[q];
+        if (j & 1) {
+            qxp[j / 2].y = a;
+            qyp[j / 2].y = b;
+            nsp[j / 2].y = o.neg_s;
+            ccp[j / 2].y = o.c;
+        } else {
+            qxp[j / 2].x = a;
+            qyp[j / 2].x = b;
+            nsp[j / 2].x = o.neg_s;
+            ccp[j / 2].x = o.c;
+        }
         hw[j] = cw[j] = hz[j] = cz[j] = 0.0f;
     }
+    const float2 eps2 = make_float2(kEpsF32, kEpsF32);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -308,12 +363,14 @@ f32_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restric
         fence_mbar_init();
     }
     __syncthreads();
-    constexpr uint32_t kBytes = kTileF32W * sizeof(float4);
+    constexpr uint32_t kBxy = kTileF32W * sizeof(float4);
+    constexpr uint32_t kBz = kTileF32W * sizeof(float2);
     if (tid == 0) {
         for (int t = 0; t < 2 && t < ntiles; ++t) {
-            mbar_arrive_expect_tx(&bar[t], kBytes);
-            tma_load_1d(tile[t], ds.xyzw + p_begin + static_cast<int64_t>(t) * kTileF32W,
-                        kBytes, &bar[t]);
+            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileF32W;
+            mbar_arrive_expect_tx(&bar[t], kBxy + kBz);
+            tma_load_1d(txy[t], ds.nxy2 + o, kBxy, &bar[t]);
+            tma_load_1d(tz[t], ds.zz + o, kBz, &bar[t]);
         }
     }
 
@@ -330,34 +387,41 @@ f32_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restric
             break;
         }
         for (int c = 0; c < kTileF32W; c += kChunkW) {
-            float sw[Q], sz[Q];
+            float2 sw[H], sz[H];
 #pragma unroll
-            for (int j = 0; j < Q; ++j)
-                sw[j] = sz[j] = 0.0f;
-#pragma unroll 8
+            for (int h = 0; h < H; ++h)
+                sw[h] = sz[h] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
             for (int u = 0; u < kChunkW; ++u) {
-                const float4 p = tile[b][c + u];
+                const float4 p = txy[b][c + u];
+                const float2 zz = tz[b][c + u];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    const float d2 = dist2_f32(qxr[j], qyr[j], p.x, p.y);
-                    const float w = ex2_approx(__fmaf_rn(lg2_approx(d2), ns[j], cc[j]));
-                    sw[j] = __fadd_rn(sw[j], w);
-                    sz[j] = __fmaf_rn(w, p.z, sz[j]);
+                for (int h = 0; h < H; ++h) {
+                    const float2 dx = __fadd2_rn(qxp[h], make_float2(p.x, p.y));
+                    const float2 dy = __fadd2_rn(qyp[h], make_float2(p.z, p.w));
+                    const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, eps2));
+                    const float2 lg = make_float2(lg2_approx(d2.x), lg2_approx(d2.y));
+                    const float2 e = __ffma2_rn(lg, nsp[h], ccp[h]);
+                    const float2 w = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                    sw[h] = __fadd2_rn(sw[h], w);
+                    sz[h] = __ffma2_rn(w, zz, sz[h]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                kahan_add(hw[j], cw[j], sw[j]);
-                kahan_add(hz[j], cz[j], sz[j]);
+            for (int h = 0; h < H; ++h) {
+                kahan_add(hw[2 * h], cw[2 * h], sw[h].x);
+                kahan_add(hw[2 * h + 1], cw[2 * h + 1], sw[h].y);
+                kahan_add(hz[2 * h], cz[2 * h], sz[h].x);
+                kahan_add(hz[2 * h + 1], cz[2 * h + 1], sz[h].y);
             }
         }
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[b], kBytes);
-            tma_load_1d(tile[b],
-                        ds.xyzw + p_begin + static_cast<int64_t>(t + 2) * kTileF32W, kBytes,
-                        &bar[b]);
+            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileF32W;
+            mbar_arrive_expect_tx(&bar[b], kBxy + kBz);
+            tma_load_1d(txy[b], ds.nxy2 + o, kBxy, &bar[b]);
+            tma_load_1d(tz[b], ds.zz + o, kBz, &bar[b]);
         }
     }
     if (!ok)
@@ -391,12 +455,18 @@ f32_finalize_kernel(int64_t m, int S, const float *__restrict__ part_sum,
     out[q] = static_cast<float>(WZ / W);  // Eq. 1
 }
 
-constexpr int kQW32 = 4;
+constexpr int kQW32 = 8;
 
 template <int KP>
 constexpr int knn_q()
 {
     return KP <= 16 ? 4 : 2;
+}
+
+// Register list length for k: the smallest of 8, 12, 16, 32 that holds k.
+inline int kp_for(int k)
+{
+    return k <= 8 ? 8 : (k <= 12 ? 12 : (k <= 16 ? 16 : 32));
 }
 
 template <int KP, bool IDX>
@@ -450,11 +520,12 @@ int f32_w_queries_per_block()
 
 int f32_knn_slots_per_sm(int k, bool with_idx)
 {
-    if (k <= 8)
-        return knn_slots_t<8>(with_idx);
-    if (k <= 16)
-        return knn_slots_t<16>(with_idx);
-    return knn_slots_t<32>(with_idx);
+    switch (kp_for(k)) {
+    case 8: return knn_slots_t<8>(with_idx);
+    case 12: return knn_slots_t<12>(with_idx);
+    case 16: return knn_slots_t<16>(with_idx);
+    default: return knn_slots_t<32>(with_idx);
+    }
 }
 
 int f32_w_slots_per_sm()
@@ -468,14 +539,20 @@ cudaError_t launch_f32_knn(const DatasetDev &ds, const Plan &pl, const float *qx
                            const float *qy, int k, const Scratch &sc, int *err,
                            cudaStream_t st)
 {
-    if (k <= 8)
+    switch (kp_for(k)) {
+    case 8:
         return pl.with_idx ? launch_knn_t<8, true>(ds, pl, qx, qy, k, sc, err, st)
                            : launch_knn_t<8, false>(ds, pl, qx, qy, k, sc, err, st);
-    if (k <= 16)
+    case 12:
+        return pl.with_idx ? launch_knn_t<12, true>(ds, pl, qx, qy, k, sc, err, st)
+                           : launch_knn_t<12, false>(ds, pl, qx, qy, k, sc, err, st);
+    case 16:
         return pl.with_idx ? launch_knn_t<16, true>(ds, pl, qx, qy, k, sc, err, st)
                            : launch_knn_t<16, false>(ds, pl, qx, qy, k, sc, err, st);
-    return pl.with_idx ? launch_knn_t<32, true>(ds, pl, qx, qy, k, sc, err, st)
-                       : launch_knn_t<32, false>(ds, pl, qx, qy, k, sc, err, st);
+    default:
+        return pl.with_idx ? launch_knn_t<32, true>(ds, pl, qx, qy, k, sc, err, st)
+                           : launch_knn_t<32, false>(ds, pl, qx, qy, k, sc, err, st);
+    }
 }
 
 cudaError_t launch_f32_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
