@@ -146,8 +146,9 @@ int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, co
                              int64_t m, const aidw_params *p, float *out, void *stream);
 
 /* ---- batched launch (many datasets in one persistent kernel) -------------------------- */
-/* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays) and params.
- * All entries of one batch share the precision AIDW_F32C. */
+/* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays of the context's
+ * device, float) and its parameters (precision must be AIDW_F32C; k and levels may differ per
+ * item). The kNN index output is not available in batches. */
 typedef struct aidw_batch_item {
     aidw_dataset ds;
     const float *qx, *qy;
@@ -157,11 +158,23 @@ typedef struct aidw_batch_item {
     float *out_alpha; /* nullable */
 } aidw_batch_item;
 
-/* Runs every item through the persistent work-queue kernels on `stream` (stream-ordered).
- * Each item's results equal those of aidw_interpolate on the same inputs within the FP32
- * tolerance, whatever else is in the batch. */
+/* Runs every item through one persistent work-queue kernel on `stream` (stream-ordered; the
+ * item arrays must stay valid until the stream reaches the work). Items are cut into units
+ * that depend only on the item, so each item's result is bit-identical whatever else is in the
+ * batch, and equal to aidw_interpolate's within the FP32 tolerance. Errors: INVALID_ARG (bad
+ * item, host array), NOT_FOUND (dataset), OOM (scratch). */
 int aidw_interpolate_batch(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count,
                            void *stream);
+
+/* A prepared batch: the item table, work list and scratch are built once and the counter reset
+ * plus the persistent kernel are captured as one CUDA graph; aidw_batch_launch replays it (the
+ * caller may rewrite query contents in place between launches). aidw_batch_destroy waits for
+ * the device and frees the batch. */
+typedef struct aidw_batch aidw_batch;
+int aidw_batch_create(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count,
+                      aidw_batch **out);
+int aidw_batch_launch(aidw_ctx *ctx, aidw_batch *batch, void *stream);
+int aidw_batch_destroy(aidw_ctx *ctx, aidw_batch *batch);
 
 /* ---- serving: asynchronous requests with continuous batching --------------------------- */
 /* Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host

@@ -84,6 +84,9 @@ SIGNATURES = {
     "aidw_idw": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _D, _I32, _P, _P]),
     "aidw_interpolate_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P]),
     "aidw_interpolate_batch": (ctypes.c_int, [_P, _P, _I32, _P]),
+    "aidw_batch_create": (ctypes.c_int, [_P, _P, _I32, _P]),
+    "aidw_batch_launch": (ctypes.c_int, [_P, _P, _P]),
+    "aidw_batch_destroy": (ctypes.c_int, [_P, _P]),
     "aidw_submit": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "aidw_poll": (ctypes.c_int, [_P, _I64, _P]),
     "aidw_wait": (ctypes.c_int, [_P, _I64, _I64]),
@@ -190,6 +193,22 @@ class Dataset:
             self.handle = 0
 
 
+class PreparedBatch:
+    """A batch whose work list and scratch are built once and replayed as a CUDA graph."""
+
+    def __init__(self, ctx: "Context", handle, items):
+        self.ctx, self.handle, self.items = ctx, handle, items
+
+    def launch(self, stream=None):
+        st = _stream_of(self.items[0][1], stream) if self.items else 0
+        _check(self.ctx.lib.aidw_batch_launch(self.ctx.ptr, self.handle, st), "batch_launch")
+
+    def destroy(self):
+        if self.handle:
+            _check(self.ctx.lib.aidw_batch_destroy(self.ctx.ptr, self.handle), "batch_destroy")
+            self.handle = None
+
+
 class Context:
     """One library context on one CUDA device (``aidw_init`` / ``aidw_shutdown``)."""
 
@@ -275,10 +294,9 @@ class Context:
                                  po, _stream_of(qx, stream)), "aidw_idw")
         return out
 
-    def interpolate_batch(self, items, stream=None):
-        """items: list of (Dataset, qx, qy, Params, out, out_alpha|None) with CUDA tensors."""
-        arr = (BatchItem * len(items))()
-        keep = []
+    @staticmethod
+    def _batch_items(items):
+        arr = (BatchItem * max(1, len(items)))()
         for i, (ds, qx, qy, p, out, oa) in enumerate(items):
             arr[i].ds = ds.handle
             arr[i].qx = qx.data_ptr()
@@ -287,10 +305,21 @@ class Context:
             arr[i].params = p
             arr[i].out = out.data_ptr()
             arr[i].out_alpha = oa.data_ptr() if oa is not None else None
-            keep.append((qx, qy, out, oa))
+        return arr
+
+    def interpolate_batch(self, items, stream=None):
+        """items: list of (Dataset, qx, qy, Params, out, out_alpha|None) with CUDA tensors."""
+        arr = self._batch_items(items)
         st = _stream_of(items[0][1], stream) if items else 0
         _check(self.lib.aidw_interpolate_batch(self.ptr, arr, len(items), st),
                "aidw_interpolate_batch")
+
+    def batch_create(self, items) -> "PreparedBatch":
+        arr = self._batch_items(items)
+        h = ctypes.c_void_p()
+        _check(self.lib.aidw_batch_create(self.ptr, arr, len(items), ctypes.byref(h)),
+               "aidw_batch_create")
+        return PreparedBatch(self, h, items)
 
     # -- serving --
     def submit(self, ds: Dataset, qx, qy, params: Params, out, out_alpha=None, out_knn=None):

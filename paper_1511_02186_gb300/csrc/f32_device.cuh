@@ -1,0 +1,473 @@
+// Device-side building blocks of the FP32 ("F32C") path, shared by the per-call grid kernels
+// (kernels_f32.cu) and the persistent batched kernel (batched.cu).
+//
+// Phase 1 (Sec. 2.2 Step 1; kNN procedure of Sec. 3.1.2) and phase 2 (Eq. 1 over all data
+// points, Sec. 3.2.1) are two all-pairs scans of the data points against blocks of queries. A
+// unit of work is one (query block, data split): 128 threads, each holding Q queries in
+// registers as Q/2 packed pairs, stream the split's data tiles through shared memory (one TMA
+// bulk copy per tile into a double buffer completed on an mbarrier) and read every data point
+// as a broadcast.
+#pragma once
+
+#include <math_constants.h>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+namespace f32dev {
+
+constexpr int kChunkKnn = 8;  // points between neighbour-list threshold checks
+constexpr int kChunkW = 32;   // points summed in plain FP32 before a Kahan merge
+constexpr float kFilterMargin = 1.0f + 9.5367431640625e-07f;  // 1 + 2^-20
+
+// Squared distance from negated data coordinates: q + (-p) is exactly q - p.
+__device__ __forceinline__ float dist2_neg(float qx, float qy, float npx, float npy)
+{
+    const float dx = __fadd_rn(qx, npx);
+    const float dy = __fadd_rn(qy, npy);
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, kEpsF32));
+}
+
+// Inserts v (< L[KP-1]) into the ascending register list L, after any equal entries.
+template <int KP>
+__device__ __forceinline__ void list_insert(float (&L)[KP], float v)
+{
+    L[KP - 1] = v;
+#pragma unroll
+    for (int i = KP - 1; i > 0; --i) {
+        const float a = L[i - 1], b = L[i];
+        L[i - 1] = fminf(a, b);
+        L[i] = fmaxf(a, b);
+    }
+}
+
+// Shared-memory index list of one query of one thread: entry i at base[i * kThreads].
+// Moves entries [pos, KP-1) up by one and writes id at pos, where pos is the number of
+// current entries (before insertion) not greater than v among the first KP-1.
+template <int KP>
+__device__ __forceinline__ void index_insert(const float (&L)[KP], int32_t *base, float v,
+                                             int32_t id)
+{
+    int pos = 0;
+#pragma unroll
+    for (int i = 0; i < KP - 1; ++i)
+        pos += (L[i] <= v) ? 1 : 0;
+    for (int i = KP - 1; i > pos; --i)
+        base[i * kThreads] = base[(i - 1) * kThreads];
+    base[pos * kThreads] = id;
+}
+
+__device__ __forceinline__ float neg_filter_threshold(float kth)
+{
+    return -(kth * kFilterMargin);
+}
+
+__device__ __forceinline__ uint32_t sign_or3(uint32_t acc, float a, float b)
+{
+    return acc | __float_as_uint(a) | __float_as_uint(b);
+}
+
+// A CTA's tile stream: two shared-memory buffers with one mbarrier each. `seq` counts the
+// tiles consumed since the barriers were initialised, so the tile with sequence number s lands
+// in buffer s & 1 and completes phase (s >> 1) & 1 of that buffer's barrier. Every unit drains
+// its own tiles before it returns, so units can follow one another on the same barriers.
+struct TileSeq {
+    uint64_t *bar;
+    uint32_t seq;
+};
+
+// Bounded wait for the tiles still in flight after an abandoned scan (tiles t, t+1).
+__device__ __forceinline__ void drain(TileSeq &ts, int t, int ntiles)
+{
+    for (int u = t; u < ntiles && u < t + 2; ++u) {
+        const uint32_t sq = ts.seq + u;
+        (void)mbar_wait(&ts.bar[sq & 1], (sq >> 1) & 1);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 1 unit: neighbour lists of Q * kThreads queries over data points [p_begin, p_end).
+//
+// The hot loop evaluates, with FP32x2 instructions, v = dx^2 + (dy^2 - T') for two queries at a
+// time, where T' is the query's current k-th squared distance enlarged by 2^-20 (relative), and
+// ORs the sign bits of v per query over an 8-point chunk. A negative v is necessary for a point
+// to enter the list: if the exact FP32 distance d2 = fl(dx^2 + fl(dy^2)) is below T then the
+// real dx^2 + dy^2 is below T (1 + 2^-23), and v, computed with at most u T' of rounding error
+// (u = 2^-24), stays negative. Only for a query whose sign bit is set is the chunk rescanned
+// with the exact distance, which alone decides insertion; the lists are therefore exactly those
+// of the plain scan. Returns false if a tile wait timed out (the error word is then set).
+// ---------------------------------------------------------------------------------------------
+template <int KP, int Q, bool IDX>
+__device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_t qbase,
+                                         int64_t p_begin, int64_t p_end,
+                                         const float *__restrict__ qx,
+                                         const float *__restrict__ qy, int k, int s,
+                                         float *__restrict__ part_d2,
+                                         int32_t *__restrict__ part_idx, int *__restrict__ err,
+                                         float4 (*tile)[kTileF32Knn], TileSeq &ts,
+                                         int32_t *idx_smem)
+{
+    static_assert(Q % 2 == 0, "queries are processed in packed pairs");
+    constexpr int H = Q / 2;
+    const int tid = threadIdx.x;
+    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF32Knn);
+
+    float2 qxp[H], qyp[H], nthr[H];
+    float L[Q][KP];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        const float a = qx[q], b = qy[q];
+        if (j & 1) {
+            qxp[j / 2].y = a;
+            qyp[j / 2].y = b;
+        } else {
+            qxp[j / 2].x = a;
+            qyp[j / 2].x = b;
+        }
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+            L[j][i] = (i < KP - k) ? -CUDART_INF_F : CUDART_INF_F;
+        if (IDX) {
+#pragma unroll
+            for (int i = 0; i < KP; ++i)
+                idx_smem[(j * KP + i) * kThreads + tid] = -1;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        nthr[h] = make_float2(-CUDART_INF_F, -CUDART_INF_F);
+
+    constexpr uint32_t kBytes = kTileF32Knn * sizeof(float4);
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < ntiles; ++t) {
+            const uint32_t b = (ts.seq + t) & 1;
+            mbar_arrive_expect_tx(&ts.bar[b], kBytes);
+            tma_load_1d(tile[b], ds.nxy2 + p_begin + static_cast<int64_t>(t) * kTileF32Knn,
+                        kBytes, &ts.bar[b]);
+        }
+    }
+
+    for (int t = 0; t < ntiles; ++t) {
+        const uint32_t sq = ts.seq + t;
+        const int b = sq & 1;
+        const bool got = mbar_wait(&ts.bar[b], (sq >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                atomicOr(err, kErrTimeout);
+                drain(ts, t, ntiles);
+            }
+            ts.seq += ntiles;
+            return false;
+        }
+        const float4 *tb = tile[b];
+        const int64_t pbase = p_begin + static_cast<int64_t>(t) * kTileF32Knn;
+        for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
+            uint32_t acc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                acc[j] = 0u;
+#pragma unroll
+            for (int u = 0; u < kChunkKnn; u += 2) {
+                const float4 pa = tb[c + u];
+                const float4 pb = tb[c + u + 1];
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float2 dxa = __fadd2_rn(qxp[h], make_float2(pa.x, pa.y));
+                    const float2 dya = __fadd2_rn(qyp[h], make_float2(pa.z, pa.w));
+                    const float2 va = __ffma2_rn(dxa, dxa, __ffma2_rn(dya, dya, nthr[h]));
+                    const float2 dxb = __fadd2_rn(qxp[h], make_float2(pb.x, pb.y));
+                    const float2 dyb = __fadd2_rn(qyp[h], make_float2(pb.z, pb.w));
+                    const float2 vb = __ffma2_rn(dxb, dxb, __ffma2_rn(dyb, dyb, nthr[h]));
+                    acc[2 * h] = sign_or3(acc[2 * h], va.x, vb.x);
+                    acc[2 * h + 1] = sign_or3(acc[2 * h + 1], va.y, vb.y);
+                }
+            }
+            uint32_t any = 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                any |= acc[j];
+            if (static_cast<int32_t>(any) < 0) {
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    if (static_cast<int32_t>(acc[j]) < 0) {
+                        const float qxj = (j & 1) ? qxp[j / 2].y : qxp[j / 2].x;
+                        const float qyj = (j & 1) ? qyp[j / 2].y : qyp[j / 2].x;
+#pragma unroll 1
+                        for (int u = 0; u < kChunkKnn; ++u) {
+                            const float4 p = tb[c + u];
+                            const float d = dist2_neg(qxj, qyj, p.x, p.z);
+                            if (d < L[j][KP - 1]) {
+                                if (IDX)
+                                    index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
+                                                     d, static_cast<int32_t>(pbase + c + u));
+                                list_insert<KP>(L[j], d);
+                            }
+                        }
+                        const float nt = neg_filter_threshold(L[j][KP - 1]);
+                        if (j & 1)
+                            nthr[j / 2].y = nt;
+                        else
+                            nthr[j / 2].x = nt;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < ntiles) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&ts.bar[b], kBytes);
+            tma_load_1d(tile[b], ds.nxy2 + pbase + 2 * kTileF32Knn, kBytes, &ts.bar[b]);
+        }
+    }
+    ts.seq += ntiles;
+
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = qbase + j * kThreads + tid;
+        if (q >= m)
+            continue;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            const int r = i - (KP - k);
+            if (r >= 0) {
+                const int64_t o = (static_cast<int64_t>(s) * k + r) * m + q;
+                part_d2[o] = L[j][i];
+                if (IDX)
+                    part_idx[o] = idx_smem[(j * KP + i) * kThreads + tid];
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Selection of one query: merge the S split lists (ties to the lower index), r_obs (Eq. 3) as an
+// FP32 pairwise sum of the k distances, R (Eq. 4 with r_exp of Eq. 2), mu (Eq. 5) and alpha
+// (Eq. 6) in FP64, then the phase-2 parameters. Split lists are read with L2-coherent loads so
+// that a consumer on another SM sees a producer's results after the counter handshake.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k, double r_exp,
+                                             const AlphaMap &am, const float *part_d2,
+                                             const int32_t *part_idx, QParamF32 *qp,
+                                             float *out_alpha, int32_t *out_knn)
+{
+    int cur[kMaxSplits];
+    float hd[kMaxSplits];
+    int32_t hi[kMaxSplits];
+    for (int s = 0; s < S; ++s) {
+        cur[s] = 0;
+        const int64_t o = static_cast<int64_t>(s) * k * m + q;
+        hd[s] = __ldcg(part_d2 + o);
+        hi[s] = part_idx ? __ldcg(part_idx + o) : 0;
+    }
+    float d[AIDW_MAX_K];
+    for (int r = 0; r < k; ++r) {
+        int bs = 0;
+        for (int s = 1; s < S; ++s)
+            if (hd[s] < hd[bs] || (hd[s] == hd[bs] && hi[s] < hi[bs]))
+                bs = s;
+        d[r] = hd[bs];
+        if (out_knn)
+            out_knn[q * k + r] = hi[bs];
+        if (++cur[bs] < k) {
+            const int64_t o = (static_cast<int64_t>(bs) * k + cur[bs]) * m + q;
+            hd[bs] = __ldcg(part_d2 + o);
+            hi[bs] = part_idx ? __ldcg(part_idx + o) : 0;
+        } else {
+            hd[bs] = CUDART_INF_F;
+            hi[bs] = INT32_MAX;
+        }
+    }
+    const float d1 = d[0];
+    // Eq. 3: mean of the k distances; sqrt of (d2 - eps) undoes the coincidence offset.
+    float v[AIDW_MAX_K];
+    for (int r = 0; r < k; ++r)
+        v[r] = __fsqrt_rn(__fsub_rn(d[r], kEpsF32));
+    for (int stride = 1; stride < k; stride *= 2)
+        for (int i = 0; i + stride < k; i += 2 * stride)
+            v[i] = __fadd_rn(v[i], v[i + stride]);
+    const double r_obs = static_cast<double>(v[0]) / k;
+    const double R = r_obs / r_exp;           // Eq. 4
+    const double mu = membership_eq5(R, am);  // Eq. 5
+    const double alpha = alpha_eq6(mu, am);   // Eq. 6
+
+    const float L1 = lg2_approx(d1);
+    QParamF32 o;
+    if (d1 == kEpsF32) {
+        // Coincident query: weight 1 on every coincident point, 0 elsewhere.
+        o.neg_s = -kCoincScaleF32;
+        o.c = kCoincScaleF32 * L1;
+    } else {
+        const float sh = static_cast<float>(0.5 * alpha);
+        o.neg_s = -sh;
+        o.c = sh * L1;
+    }
+    qp[q] = o;
+    if (out_alpha)
+        out_alpha[q] = static_cast<float>(alpha);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 2 unit: compensated sums of w and w z for Q * kThreads queries over [p_begin, p_end).
+// Distances, power scale and both sums run as FP32x2 instructions on query pairs; lg2 and ex2
+// run on the MUFU. w = 2^(s (L1 - log2 d2)) with s = alpha/2 and L1 = log2 of the nearest
+// squared distance, i.e. (d1/d)^alpha <= 1: the ratio of Eq. 1 is unchanged and nothing
+// overflows. Each thread sums kChunkW points per query in plain FP32 and merges the chunk sums
+// by Kahan steps; the partial sums of the split go to part_sum[s][0..3][q].
+// ---------------------------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, int64_t qbase,
+                                             int64_t p_begin, int64_t p_end,
+                                             const float *__restrict__ qx,
+                                             const float *__restrict__ qy,
+                                             const QParamF32 *qp, int s,
+                                             float *__restrict__ part_sum,
+                                             int *__restrict__ err,
+                                             float4 (*txy)[kTileF32W],
+                                             float2 (*tz)[kTileF32W], TileSeq &ts)
+{
+    static_assert(Q % 2 == 0, "queries are processed in packed pairs");
+    constexpr int H = Q / 2;
+    const int tid = threadIdx.x;
+    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF32W);
+
+    float2 qxp[H], qyp[H], nsp[H], ccp[H];
+    float hw[Q], cw[Q], hz[Q], cz[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        const float2 o = __ldcg(reinterpret_cast<const float2 *>(qp + q));
+        const float a = qx[q], b = qy[q];
+        if (j & 1) {
+            qxp[j / 2].y = a;
+            qyp[j / 2].y = b;
+            nsp[j / 2].y = o.x;
+            ccp[j / 2].y = o.y;
+        } else {
+            qxp[j / 2].x = a;
+            qyp[j / 2].x = b;
+            nsp[j / 2].x = o.x;
+            ccp[j / 2].x = o.y;
+        }
+        hw[j] = cw[j] = hz[j] = cz[j] = 0.0f;
+    }
+    const float2 eps2 = make_float2(kEpsF32, kEpsF32);
+
+    constexpr uint32_t kBxy = kTileF32W * sizeof(float4);
+    constexpr uint32_t kBz = kTileF32W * sizeof(float2);
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < ntiles; ++t) {
+            const uint32_t b = (ts.seq + t) & 1;
+            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileF32W;
+            mbar_arrive_expect_tx(&ts.bar[b], kBxy + kBz);
+            tma_load_1d(txy[b], ds.nxy2 + o, kBxy, &ts.bar[b]);
+            tma_load_1d(tz[b], ds.zz + o, kBz, &ts.bar[b]);
+        }
+    }
+
+    for (int t = 0; t < ntiles; ++t) {
+        const uint32_t sq = ts.seq + t;
+        const int b = sq & 1;
+        const bool got = mbar_wait(&ts.bar[b], (sq >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                atomicOr(err, kErrTimeout);
+                drain(ts, t, ntiles);
+            }
+            ts.seq += ntiles;
+            return false;
+        }
+        for (int c = 0; c < kTileF32W; c += kChunkW) {
+            float2 sw[H], sz[H];
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+                sw[h] = sz[h] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+            for (int u = 0; u < kChunkW; ++u) {
+                const float4 p = txy[b][c + u];
+                const float2 zz = tz[b][c + u];
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float2 dx = __fadd2_rn(qxp[h], make_float2(p.x, p.y));
+                    const float2 dy = __fadd2_rn(qyp[h], make_float2(p.z, p.w));
+                    const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, eps2));
+                    const float2 lg = make_float2(lg2_approx(d2.x), lg2_approx(d2.y));
+                    const float2 e = __ffma2_rn(lg, nsp[h], ccp[h]);
+                    const float2 w = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                    sw[h] = __fadd2_rn(sw[h], w);
+                    sz[h] = __ffma2_rn(w, zz, sz[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                kahan_add(hw[2 * h], cw[2 * h], sw[h].x);
+                kahan_add(hw[2 * h + 1], cw[2 * h + 1], sw[h].y);
+                kahan_add(hz[2 * h], cz[2 * h], sz[h].x);
+                kahan_add(hz[2 * h + 1], cz[2 * h + 1], sz[h].y);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < ntiles) {
+            fence_proxy_async_smem();
+            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileF32W;
+            mbar_arrive_expect_tx(&ts.bar[b], kBxy + kBz);
+            tma_load_1d(txy[b], ds.nxy2 + o, kBxy, &ts.bar[b]);
+            tma_load_1d(tz[b], ds.zz + o, kBz, &ts.bar[b]);
+        }
+    }
+    ts.seq += ntiles;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = qbase + j * kThreads + tid;
+        if (q >= m)
+            continue;
+        float *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
+        o[0] = hw[j];
+        o[m] = -cw[j];
+        o[2 * m] = hz[j];
+        o[3 * m] = -cz[j];
+    }
+    return true;
+}
+
+// Eq. 1 for one query: merge the S splits' compensated sums in FP64 and divide.
+__device__ __forceinline__ float finalize_query(int64_t q, int64_t m, int S,
+                                                const float *part_sum)
+{
+    double W = 0.0, WZ = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const float *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
+        W += static_cast<double>(__ldcg(o)) + static_cast<double>(__ldcg(o + m));
+        WZ += static_cast<double>(__ldcg(o + 2 * m)) + static_cast<double>(__ldcg(o + 3 * m));
+    }
+    return static_cast<float>(WZ / W);
+}
+
+// Shared-memory barrier set-up common to every kernel that streams tiles.
+__device__ __forceinline__ void init_tile_barriers(uint64_t *bar)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+template <int KP>
+constexpr int knn_q()
+{
+    return KP <= 16 ? 4 : 2;
+}
+
+// Register list length for k: the smallest of 8, 12, 16, 32 that holds k.
+__host__ __device__ inline int kp_for(int k)
+{
+    return k <= 8 ? 8 : (k <= 12 ? 12 : (k <= 16 ? 16 : 32));
+}
+
+constexpr int kQW32 = 8;  // queries per thread in phase 2
+
+}  // namespace f32dev
+}  // namespace aidw

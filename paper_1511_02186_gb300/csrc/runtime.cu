@@ -107,23 +107,6 @@ using namespace aidw;
 
 extern "C" {
 
-int aidw_interpolate_batch(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count,
-                           void *stream)
-{
-    if (!ctx || (count > 0 && !items) || count < 0)
-        return AIDW_ERR_INVALID_ARG;
-    for (int32_t i = 0; i < count; ++i) {
-        if (items[i].params.precision != AIDW_F32C)
-            return AIDW_ERR_INVALID_ARG;
-        int rc = interpolate_impl(ctx, items[i].ds, items[i].qx, items[i].qy, items[i].m,
-                                  &items[i].params, items[i].out, items[i].out_alpha, nullptr,
-                                  static_cast<cudaStream_t>(stream), 0, 0);
-        if (rc)
-            return rc;
-    }
-    return AIDW_OK;
-}
-
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
                 const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
                 aidw_request *out_id)
