@@ -178,9 +178,13 @@ int aidw_batch_destroy(aidw_ctx *ctx, aidw_batch *batch);
 
 /* ---- serving: asynchronous requests with continuous batching --------------------------- */
 /* Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host
- * or device and must stay valid until aidw_poll/aidw_wait report completion). Requests are
- * admitted by HBM footprint and batched into persistent launches by the context's serving
- * thread, started on first use. Returns AIDW_ERR_AGAIN if the queue is full. */
+ * or device and must stay valid until aidw_poll/aidw_wait report completion). The context's
+ * serving thread, started on first use, admits queued requests in arrival order while their
+ * device footprint fits the serving budget and packs them into persistent batch launches
+ * (continuous batching: a new launch starts on another stream while earlier ones still run).
+ * An FP32 request's result does not depend on what it was batched with. FP64 requests and
+ * requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests)
+ * is full; a request larger than the whole budget finishes with AIDW_ERR_OOM. */
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
                 const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
                 aidw_request *out_id);
@@ -197,6 +201,29 @@ int aidw_request_latency_us(aidw_ctx *ctx, aidw_request id, double *latency_us);
 
 /* Forgets a finished request (its handle becomes unknown); AIDW_PENDING if not finished. */
 int aidw_release_request(aidw_ctx *ctx, aidw_request id);
+
+/* Shapes the serving runtime; call before the first aidw_submit (INVALID_ARG afterwards).
+ * inflight_bytes: device memory that admitted requests may hold at once (0: half of the
+ * context's budget, or 8 GiB without one); max_batch_requests: requests per launch (0: 256);
+ * streams: launches that may run at once (0: 2, at most 8). */
+int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_batch_requests,
+                           int32_t streams);
+
+typedef struct aidw_serving_stats {
+    int64_t submitted;       /* requests accepted by aidw_submit */
+    int64_t completed;       /* finished with AIDW_OK */
+    int64_t failed;          /* finished with an error status */
+    int64_t rejected_again;  /* aidw_submit calls refused with AIDW_ERR_AGAIN */
+    int64_t launches;        /* device launches (batches and lone requests) */
+    int64_t batched_requests;        /* requests that went through batch launches */
+    int32_t max_concurrent_launches; /* most launches in flight at once */
+    int32_t reserved;
+    int64_t queued;          /* requests waiting for admission now */
+    size_t in_flight_bytes;  /* device bytes held by admitted requests now */
+    size_t budget_bytes;     /* admission budget */
+} aidw_serving_stats;
+
+int aidw_serving_get_stats(aidw_ctx *ctx, aidw_serving_stats *out);
 
 /* ---- diagnostics ---------------------------------------------------------------------- */
 const char *aidw_status_string(int status);

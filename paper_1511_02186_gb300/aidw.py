@@ -65,6 +65,15 @@ class PipeRates(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class ServingStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("rejected_again", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
+                ("max_concurrent_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("queued", ctypes.c_int64), ("in_flight_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("ds", ctypes.c_int64), ("qx", ctypes.c_void_p), ("qy", ctypes.c_void_p),
                 ("m", ctypes.c_int64), ("params", Params), ("out", ctypes.c_void_p),
@@ -92,6 +101,8 @@ SIGNATURES = {
     "aidw_wait": (ctypes.c_int, [_P, _I64, _I64]),
     "aidw_request_latency_us": (ctypes.c_int, [_P, _I64, _P]),
     "aidw_release_request": (ctypes.c_int, [_P, _I64]),
+    "aidw_serving_configure": (ctypes.c_int, [_P, ctypes.c_size_t, _I32, _I32]),
+    "aidw_serving_get_stats": (ctypes.c_int, [_P, _P]),
     "aidw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "aidw_check_device_errors": (ctypes.c_int, [_P]),
     "aidw_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -166,6 +177,15 @@ def _prep(a, dtype):
     return arr, arr.ctypes.data
 
 
+def _prep_out(a, dtype):
+    """Pointer to an output array that the library writes in place (no conversion allowed)."""
+    if _is_torch(a):
+        return _prep(a, dtype)[1]
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+        raise TypeError(f"output must be a contiguous {dtype} array")
+    return a.ctypes.data
+
+
 def _out_like(q, shape, dtype):
     if _is_torch(q):
         import torch
@@ -218,6 +238,7 @@ class Context:
         _check(self.lib.aidw_init(ctypes.byref(self._ptr), int(device), int(hbm_budget)),
                "aidw_init")
         self.device = device
+        self._keep = {}
 
     @property
     def ptr(self):
@@ -229,6 +250,7 @@ class Context:
         if self._ptr:
             self.lib.aidw_shutdown(self._ptr)
             self._ptr = ctypes.c_void_p()
+            self._keep.clear()
 
     def __enter__(self):
         return self
@@ -323,15 +345,20 @@ class Context:
 
     # -- serving --
     def submit(self, ds: Dataset, qx, qy, params: Params, out, out_alpha=None, out_knn=None):
+        """Queue a request; returns (status, request id). The query arrays are kept alive by
+        the context until the request is released; output arrays must already have the right
+        dtype and be contiguous (they are written in place when the request completes)."""
         fdt = "f8" if params.precision == F64 else "f4"
-        _, pqx = _prep(qx, fdt)
-        _, pqy = _prep(qy, fdt)
-        _, po = _prep(out, fdt)
-        pa = None if out_alpha is None else _prep(out_alpha, "f4")[1]
-        pn = None if out_knn is None else _prep(out_knn, "i4")[1]
+        kqx, pqx = _prep(qx, fdt)
+        kqy, pqy = _prep(qy, fdt)
+        po = _prep_out(out, fdt)
+        pa = None if out_alpha is None else _prep_out(out_alpha, "f4")
+        pn = None if out_knn is None else _prep_out(out_knn, "i4")
         rid = ctypes.c_int64()
-        rc = self.lib.aidw_submit(self.ptr, ds.handle, pqx, pqy, int(len(qx)),
+        rc = self.lib.aidw_submit(self.ptr, ds.handle, pqx, pqy, int(len(kqx)),
                                   ctypes.byref(params), po, pa, pn, ctypes.byref(rid))
+        if rc == OK:
+            self._keep[rid.value] = (kqx, kqy, out, out_alpha, out_knn)
         return rc, rid.value
 
     def poll(self, rid: int):
@@ -348,7 +375,21 @@ class Context:
         return v.value
 
     def release(self, rid: int) -> int:
-        return self.lib.aidw_release_request(self.ptr, int(rid))
+        rc = self.lib.aidw_release_request(self.ptr, int(rid))
+        if rc == OK:
+            self._keep.pop(int(rid), None)
+        return rc
+
+    def serving_configure(self, inflight_bytes: int = 0, max_batch_requests: int = 0,
+                          streams: int = 0):
+        _check(self.lib.aidw_serving_configure(self.ptr, int(inflight_bytes),
+                                               int(max_batch_requests), int(streams)),
+               "serving_configure")
+
+    def serving_stats(self) -> ServingStats:
+        s = ServingStats()
+        _check(self.lib.aidw_serving_get_stats(self.ptr, ctypes.byref(s)), "serving_stats")
+        return s
 
     # -- diagnostics --
     def set_profiling(self, on: bool):

@@ -42,4 +42,23 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
 // Stops the serving thread (waits for admitted work) and frees its state; null is a no-op.
 void serving_stop(ServingRuntime *rt);
 
+// A built batch (batched.cu): device tables, work list, counters and scratch in one block.
+struct BatchState {
+    void *block = nullptr;
+    size_t bytes = 0;
+    void *d_items = nullptr;  // item table
+    void *d_units = nullptr;  // work list
+    uint32_t *d_counters = nullptr;  // [0] work counter, then per-item counters
+    size_t counter_bytes = 0;
+    int n_units = 0;
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
+                BatchState *bs);
+int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st);
+void batch_release(aidw_ctx *ctx, BatchState *bs, cudaStream_t st);
+// Device bytes one batch item of m queries against n_pad points with k neighbours needs.
+size_t batch_item_bytes(int64_t n_pad, int64_t m, int k);
+
 }  // namespace aidw

@@ -217,17 +217,17 @@ int batch_grid(int sm_count)
 
 }  // namespace
 
-struct BatchState {
-    void *block = nullptr;
-    size_t bytes = 0;
-    BatchItemDev *d_items = nullptr;
-    WorkUnit *d_units = nullptr;
-    uint32_t *d_counters = nullptr;  // [0] = work counter, then every item's counters
-    size_t counter_bytes = 0;
-    int n_units = 0;
-    int grid = 0;
-    cudaGraphExec_t graph = nullptr;
-};
+size_t batch_item_bytes(int64_t n_pad, int64_t m, int k)
+{
+    const int kp = kp_for(k);
+    const PassPlan pk = batch_pass(m, n_pad, kThreads * (kp <= 16 ? 4 : 2), kBatchKnnSplit);
+    const PassPlan pw = batch_pass(m, n_pad, kThreads * kQW32, kBatchWSplit);
+    const size_t mm = static_cast<size_t>(m);
+    return align256(pk.splits * static_cast<size_t>(k) * mm * sizeof(float)) +
+           align256(mm * sizeof(QParamF32)) + align256(pw.splits * 4 * mm * sizeof(float)) +
+           sizeof(uint32_t) * (pk.qblocks + 1 + pw.qblocks) + sizeof(BatchItemDev) +
+           sizeof(WorkUnit) * (pk.qblocks * (pk.splits + 1) + pw.qblocks * (pw.splits + 1));
+}
 
 // Validates the items and builds the device tables of a batch in library memory.
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
@@ -308,8 +308,8 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     if (rc)
         return rc;
     char *base = static_cast<char *>(bs->block);
-    bs->d_items = reinterpret_cast<BatchItemDev *>(base);
-    bs->d_units = reinterpret_cast<WorkUnit *>(base + b_items);
+    bs->d_items = base;
+    bs->d_units = base + b_items;
     bs->d_counters = reinterpret_cast<uint32_t *>(base + b_items + b_units);
     bs->counter_bytes = cnt_total;
     char *scratch = base + b_items + b_units + b_cnt;
@@ -354,8 +354,9 @@ int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st)
         return AIDW_OK;
     if (cudaMemsetAsync(bs.d_counters, 0, bs.counter_bytes, st) != cudaSuccess)
         return AIDW_ERR_CUDA;
-    f32_batch_kernel<<<bs.grid, kThreads, 0, st>>>(bs.d_items, bs.d_units, bs.n_units,
-                                                   bs.d_counters, ctx_err_word(ctx));
+    f32_batch_kernel<<<bs.grid, kThreads, 0, st>>>(
+        static_cast<const BatchItemDev *>(bs.d_items), static_cast<const WorkUnit *>(bs.d_units),
+        bs.n_units, bs.d_counters, ctx_err_word(ctx));
     return cudaGetLastError() == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
 }
 

@@ -1,28 +1,72 @@
-// Batching and serving layer over the one-shot interpolation path.
+// Serving layer: asynchronous requests with continuous batching.
+//
+// aidw_submit queues a request and returns a handle. A worker thread owned by the context
+// admits queued requests in arrival order while their device footprint (batch scratch plus
+// staging of host arrays) fits the serving budget, packs them into one persistent batch launch
+// (batched.cu) on one of several streams, and goes on admitting newly arrived requests into the
+// next launch on another stream while earlier launches still run, so their work overlaps on the
+// device. Completion is observed with events; the footprint is then returned to the budget.
+// FP32 requests without a kNN output go through the batch kernel, whose per-item result does
+// not depend on the batch composition; FP64 requests and requests asking for neighbour indices
+// run alone through the one-shot path.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "aidw_internal.cuh"
 #include "aidw_runtime.h"
 
 namespace aidw {
 
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+inline size_t align256(size_t b)
+{
+    return (b + 255) & ~static_cast<size_t>(255);
+}
+
 struct Request {
-    int64_t ds;
-    const void *qx, *qy;
-    int64_t m;
-    aidw_params p;
-    void *out;
-    float *out_alpha;
-    int32_t *out_knn;
+    int64_t ds = 0;
+    const void *qx = nullptr, *qy = nullptr;
+    int64_t m = 0;
+    aidw_params p{};
+    void *out = nullptr;
+    float *out_alpha = nullptr;
+    int32_t *out_knn = nullptr;
+    bool host_qx = false, host_qy = false, host_out = false, host_alpha = false;
+    bool solo = false;  // FP64 or kNN output: runs through the one-shot path
+    size_t footprint = 0;
     int status = AIDW_PENDING;
     bool done = false;
-    std::chrono::steady_clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_done;
 };
+
+struct Flight {
+    bool busy = false;
+    std::vector<int64_t> ids;
+    cudaEvent_t done_ev = nullptr;
+    cudaStream_t stream = nullptr;
+    void *pinned = nullptr;  // host staging (pinned), grown on demand
+    size_t pinned_bytes = 0;
+    size_t footprint = 0;
+    // Host copies to perform when the launch completes: (dst user pointer, src pinned, bytes).
+    struct CopyOut {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    };
+    std::vector<CopyOut> copy_out;
+};
+
+}  // namespace
 
 struct ServingRuntime {
     aidw_ctx *ctx = nullptr;
@@ -32,52 +76,282 @@ struct ServingRuntime {
     std::unordered_map<int64_t, Request> reqs;
     int64_t next_id = 1;
     size_t max_queue = 4096;
+    size_t budget = size_t(8) << 30;  // device bytes in flight
+    size_t in_flight = 0;
+    int max_items = 256;
+    int n_slots = 2;
+    std::vector<Flight> flights;
     bool stop = false;
     std::thread worker;
-    cudaStream_t stream = nullptr;
+    aidw_serving_stats stats{};
 };
 
 namespace {
 
+size_t request_footprint(const Request &r, int64_t n_pad)
+{
+    size_t b = batch_item_bytes(n_pad, r.m, r.p.k) + 4096;
+    const size_t m = static_cast<size_t>(r.m);
+    if (r.host_qx)
+        b += align256(4 * m);
+    if (r.host_qy)
+        b += align256(4 * m);
+    if (r.host_out)
+        b += align256(4 * m);
+    if (r.host_alpha)
+        b += align256(4 * m);
+    return b;
+}
+
+void finish(ServingRuntime *rt, const std::vector<int64_t> &ids, int status)
+{
+    const auto now = Clock::now();
+    for (int64_t id : ids) {
+        Request &r = rt->reqs[id];
+        if (r.status == AIDW_PENDING)
+            r.status = status;
+        r.done = true;
+        r.t_done = now;
+        if (r.status == AIDW_OK)
+            ++rt->stats.completed;
+        else
+            ++rt->stats.failed;
+    }
+}
+
+bool ensure_pinned(Flight &f, size_t bytes)
+{
+    if (f.pinned_bytes >= bytes)
+        return true;
+    if (f.pinned)
+        cudaFreeHost(f.pinned);
+    f.pinned = nullptr;
+    f.pinned_bytes = 0;
+    size_t cap = bytes + bytes / 2 + (1 << 20);
+    if (cudaHostAlloc(&f.pinned, cap, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    f.pinned_bytes = cap;
+    return true;
+}
+
+// Launches the batch of requests `ids` on flight slot f. Called without the runtime lock; the
+// requests are owned by this launch until completion.
+int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &rq)
+{
+    aidw_ctx *ctx = rt->ctx;
+    cudaStream_t st = f.stream;
+    // Staging sizes.
+    size_t host_bytes = 0, dev_bytes = 0;
+    for (const Request *r : rq) {
+        const size_t b = align256(4 * static_cast<size_t>(r->m));
+        const size_t h = (r->host_qx ? b : 0) + (r->host_qy ? b : 0) + (r->host_out ? b : 0) +
+                         (r->host_alpha ? b : 0);
+        host_bytes += h;
+        dev_bytes += h;
+    }
+    f.copy_out.clear();
+    if (host_bytes && !ensure_pinned(f, host_bytes))
+        return AIDW_ERR_OOM;
+    void *dstage = nullptr;
+    int rc = ctx_alloc(ctx, dev_bytes, st, &dstage);
+    if (rc)
+        return rc;
+    std::vector<aidw_batch_item> items(rq.size());
+    char *hp = static_cast<char *>(f.pinned);
+    char *dp = static_cast<char *>(dstage);
+    bool ok = true;
+    for (size_t i = 0; i < rq.size(); ++i) {
+        const Request &r = *rq[i];
+        const size_t bytes = 4 * static_cast<size_t>(r.m), b = align256(bytes);
+        aidw_batch_item &it = items[i];
+        it.ds = r.ds;
+        it.m = r.m;
+        it.params = r.p;
+        it.qx = static_cast<const float *>(r.qx);
+        it.qy = static_cast<const float *>(r.qy);
+        it.out = static_cast<float *>(r.out);
+        it.out_alpha = r.out_alpha;
+        auto stage_in = [&](const void *src, const float **dst) {
+            std::memcpy(hp, src, bytes);
+            ok &= cudaMemcpyAsync(dp, hp, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            *dst = reinterpret_cast<const float *>(dp);
+            hp += b;
+            dp += b;
+        };
+        auto stage_out = [&](void *user, float **dst) {
+            *dst = reinterpret_cast<float *>(dp);
+            f.copy_out.push_back({user, hp, bytes});
+            hp += b;
+            dp += b;
+        };
+        if (r.host_qx)
+            stage_in(r.qx, &it.qx);
+        if (r.host_qy)
+            stage_in(r.qy, &it.qy);
+        if (r.host_out)
+            stage_out(r.out, &it.out);
+        if (r.host_alpha)
+            stage_out(r.out_alpha, &it.out_alpha);
+    }
+    if (!ok) {
+        ctx_free(ctx, dstage, dev_bytes, st);
+        return AIDW_ERR_CUDA;
+    }
+    BatchState bs{};
+    rc = batch_build(ctx, items.data(), static_cast<int32_t>(items.size()), st, &bs);
+    if (rc == AIDW_OK)
+        rc = batch_enqueue(ctx, bs, st);
+    if (rc == AIDW_OK) {
+        // Device staging of outputs -> pinned host staging, in the same order as copy_out.
+        char *d = static_cast<char *>(dstage);
+        char *h = static_cast<char *>(f.pinned);
+        for (size_t i = 0; i < rq.size(); ++i) {
+            const Request &r = *rq[i];
+            const size_t bytes = 4 * static_cast<size_t>(r.m), b = align256(bytes);
+            if (r.host_qx)
+                d += b, h += b;
+            if (r.host_qy)
+                d += b, h += b;
+            if (r.host_out) {
+                cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
+                d += b, h += b;
+            }
+            if (r.host_alpha) {
+                cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
+                d += b, h += b;
+            }
+        }
+    }
+    if (bs.block)
+        batch_release(ctx, &bs, st);
+    ctx_free(ctx, dstage, dev_bytes, st);
+    if (rc == AIDW_OK && cudaEventRecord(f.done_ev, st) != cudaSuccess)
+        rc = AIDW_ERR_CUDA;
+    return rc;
+}
+
 void worker_main(ServingRuntime *rt)
 {
     cudaSetDevice(ctx_device(rt->ctx));
+    std::unique_lock<std::mutex> g(rt->mu);
     for (;;) {
-        int64_t id;
-        Request r;
-        {
-            std::unique_lock<std::mutex> g(rt->mu);
+        // 1. Completions.
+        bool any_busy = false;
+        for (Flight &f : rt->flights) {
+            if (!f.busy)
+                continue;
+            const cudaError_t q = cudaEventQuery(f.done_ev);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            int status = q == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
+            if (q != cudaSuccess)
+                cudaGetLastError();
+            for (const Flight::CopyOut &c : f.copy_out)
+                std::memcpy(c.dst, c.src, c.bytes);
+            f.copy_out.clear();
+            finish(rt, f.ids, status);
+            rt->in_flight -= f.footprint;
+            f.footprint = 0;
+            f.ids.clear();
+            f.busy = false;
+            rt->cv_done.notify_all();
+        }
+        if (rt->stop && rt->queue.empty() && !any_busy)
+            break;
+        // 2. Admission into every free slot.
+        for (Flight &f : rt->flights) {
+            if (f.busy || rt->queue.empty())
+                continue;
+            std::vector<int64_t> ids;
+            std::vector<Request *> rq;
+            size_t fp = 0;
+            while (!rt->queue.empty() && static_cast<int>(ids.size()) < rt->max_items) {
+                const int64_t id = rt->queue.front();
+                Request &r = rt->reqs[id];
+                if (r.solo) {
+                    if (!ids.empty())
+                        break;  // runs alone, next round
+                    rt->queue.pop_front();
+                    g.unlock();
+                    int rc = interpolate_impl(rt->ctx, r.ds, r.qx, r.qy, r.m, &r.p, r.out,
+                                              r.out_alpha, r.out_knn, f.stream, 0, 0);
+                    if (rc == AIDW_OK && cudaStreamSynchronize(f.stream) != cudaSuccess)
+                        rc = AIDW_ERR_CUDA;
+                    g.lock();
+                    finish(rt, {id}, rc);
+                    ++rt->stats.launches;
+                    rt->cv_done.notify_all();
+                    continue;
+                }
+                if (r.footprint > rt->budget) {
+                    rt->queue.pop_front();
+                    finish(rt, {id}, AIDW_ERR_OOM);
+                    rt->cv_done.notify_all();
+                    continue;
+                }
+                if (rt->in_flight + fp + r.footprint > rt->budget)
+                    break;  // admitted when memory frees up
+                rt->queue.pop_front();
+                ids.push_back(id);
+                rq.push_back(&r);
+                fp += r.footprint;
+            }
+            if (ids.empty())
+                continue;
+            f.busy = true;
+            f.ids = ids;
+            f.footprint = fp;
+            rt->in_flight += fp;
+            ++rt->stats.launches;
+            rt->stats.batched_requests += ids.size();
+            int live = 0;
+            for (const Flight &o : rt->flights)
+                live += o.busy ? 1 : 0;
+            if (live > rt->stats.max_concurrent_launches)
+                rt->stats.max_concurrent_launches = live;
+            g.unlock();
+            const int rc = launch_flight(rt, f, rq);
+            g.lock();
+            if (rc != AIDW_OK) {
+                finish(rt, f.ids, rc);
+                rt->in_flight -= f.footprint;
+                f.footprint = 0;
+                f.ids.clear();
+                f.busy = false;
+                f.copy_out.clear();
+                rt->cv_done.notify_all();
+            } else {
+                any_busy = true;
+            }
+        }
+        // 3. Sleep until new work or a completion is likely.
+        if (any_busy)
+            rt->cv_work.wait_for(g, std::chrono::microseconds(20));
+        else if (rt->queue.empty() && !rt->stop)
             rt->cv_work.wait(g, [&] { return rt->stop || !rt->queue.empty(); });
-            if (rt->queue.empty())
-                return;
-            id = rt->queue.front();
-            rt->queue.pop_front();
-            r = rt->reqs[id];
-        }
-        int rc = interpolate_impl(rt->ctx, r.ds, r.qx, r.qy, r.m, &r.p, r.out, r.out_alpha,
-                                  r.out_knn, rt->stream, 0, 0);
-        if (rc == AIDW_OK && cudaStreamSynchronize(rt->stream) != cudaSuccess)
-            rc = AIDW_ERR_CUDA;
-        {
-            std::lock_guard<std::mutex> g(rt->mu);
-            Request &q = rt->reqs[id];
-            q.status = rc;
-            q.done = true;
-            q.t_done = std::chrono::steady_clock::now();
-        }
-        rt->cv_done.notify_all();
     }
 }
 
 ServingRuntime *ensure_serving(aidw_ctx *ctx)
 {
+    const size_t left = ctx_budget_left(ctx);
     std::lock_guard<std::mutex> g(ctx_mutex(ctx));
     ServingRuntime *&rt = ctx_serving(ctx);
     if (!rt) {
         rt = new ServingRuntime();
         rt->ctx = ctx;
+        if (left != SIZE_MAX)
+            rt->budget = left / 2;
         cudaSetDevice(ctx_device(ctx));
-        cudaStreamCreateWithFlags(&rt->stream, cudaStreamNonBlocking);
+        rt->flights.resize(rt->n_slots);
+        for (Flight &f : rt->flights) {
+            cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming);
+        }
         rt->worker = std::thread(worker_main, rt);
     }
     return rt;
@@ -96,8 +370,16 @@ void serving_stop(ServingRuntime *rt)
     rt->cv_work.notify_all();
     if (rt->worker.joinable())
         rt->worker.join();
-    if (rt->stream)
-        cudaStreamDestroy(rt->stream);
+    for (Flight &f : rt->flights) {
+        if (f.stream)
+            cudaStreamSynchronize(f.stream);
+        if (f.pinned)
+            cudaFreeHost(f.pinned);
+        if (f.done_ev)
+            cudaEventDestroy(f.done_ev);
+        if (f.stream)
+            cudaStreamDestroy(f.stream);
+    }
     delete rt;
 }
 
@@ -106,6 +388,40 @@ void serving_stop(ServingRuntime *rt)
 using namespace aidw;
 
 extern "C" {
+
+int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_batch_requests,
+                           int32_t streams)
+{
+    if (!ctx || max_batch_requests < 0 || streams < 0 || streams > 8)
+        return AIDW_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> g(ctx_mutex(ctx));
+        if (ctx_serving(ctx))
+            return AIDW_ERR_INVALID_ARG;  // configure before the first submit
+    }
+    ServingRuntime *rt;
+    {
+        // Create stopped-free runtime with the requested shape.
+        std::lock_guard<std::mutex> g(ctx_mutex(ctx));
+        rt = new ServingRuntime();
+        rt->ctx = ctx;
+        if (inflight_bytes)
+            rt->budget = inflight_bytes;
+        if (max_batch_requests)
+            rt->max_items = max_batch_requests;
+        if (streams)
+            rt->n_slots = streams;
+        cudaSetDevice(ctx_device(ctx));
+        rt->flights.resize(rt->n_slots);
+        for (Flight &f : rt->flights) {
+            cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming);
+        }
+        ctx_serving(ctx) = rt;
+    }
+    rt->worker = std::thread(worker_main, rt);
+    return AIDW_OK;
+}
 
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
                 const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
@@ -121,26 +437,56 @@ int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, 
     int rc = validate_params(p, dev.n);
     if (rc)
         return rc;
-    if (m < 0 || (m > 0 && (!qx || !qy || !out)))
+    if (m < 0 || m > (int64_t(1) << 31) || (m > 0 && (!qx || !qy || !out)))
         return AIDW_ERR_INVALID_ARG;
+    const int device = ctx_device(ctx);
+    Request r;
+    r.ds = ds;
+    r.qx = qx;
+    r.qy = qy;
+    r.m = m;
+    r.p = *p;
+    r.out = out;
+    r.out_alpha = out_alpha;
+    r.out_knn = out_knn;
+    const int kq = pointer_kind(qx, device), kqy = pointer_kind(qy, device);
+    const int ko = pointer_kind(out, device), ka = pointer_kind(out_alpha, device);
+    if (kq < 0 || kqy < 0 || ko < 0 || ka < 0 || pointer_kind(out_knn, device) < 0)
+        return AIDW_ERR_INVALID_ARG;
+    r.host_qx = kq == 0;
+    r.host_qy = kqy == 0;
+    r.host_out = ko == 0;
+    r.host_alpha = out_alpha && ka == 0;
+    r.solo = p->precision != AIDW_F32C || out_knn != nullptr;
+    if (r.host_qx || r.host_qy) {
+        for (int64_t i = 0; i < m; ++i) {
+            const float a = static_cast<const float *>(qx)[i];
+            const float b = static_cast<const float *>(qy)[i];
+            if (!r.solo && !(std::isfinite(a) && std::isfinite(b)))
+                return AIDW_ERR_INVALID_ARG;
+        }
+    }
+    r.footprint = request_footprint(r, dev.n_pad);
     ServingRuntime *rt = ensure_serving(ctx);
     {
         std::lock_guard<std::mutex> g(rt->mu);
-        if (rt->queue.size() >= rt->max_queue)
+        if (rt->queue.size() >= rt->max_queue) {
+            ++rt->stats.rejected_again;
             return AIDW_ERR_AGAIN;
+        }
         const int64_t id = rt->next_id++;
-        Request r;
-        r.ds = ds;
-        r.qx = qx;
-        r.qy = qy;
-        r.m = m;
-        r.p = *p;
-        r.out = out;
-        r.out_alpha = out_alpha;
-        r.out_knn = out_knn;
-        r.t_submit = std::chrono::steady_clock::now();
+        r.t_submit = Clock::now();
+        if (m == 0) {
+            r.status = AIDW_OK;
+            r.done = true;
+            r.t_done = r.t_submit;
+            rt->reqs.emplace(id, r);
+            *out_id = id;
+            return AIDW_OK;
+        }
         rt->reqs.emplace(id, r);
         rt->queue.push_back(id);
+        ++rt->stats.submitted;
         *out_id = id;
     }
     rt->cv_work.notify_one();
@@ -176,12 +522,13 @@ int aidw_wait(aidw_ctx *ctx, aidw_request id, int64_t timeout_us)
     auto it = rt->reqs.find(id);
     if (it == rt->reqs.end())
         return AIDW_ERR_NOT_FOUND;
-    auto pred = [&] { return rt->reqs[id].done; };
+    Request *r = &it->second;
+    auto pred = [&] { return r->done; };
     if (timeout_us < 0)
         rt->cv_done.wait(g, pred);
     else if (!rt->cv_done.wait_for(g, std::chrono::microseconds(timeout_us), pred))
         return AIDW_ERR_TIMEOUT;
-    return rt->reqs[id].status;
+    return r->status;
 }
 
 int aidw_request_latency_us(aidw_ctx *ctx, aidw_request id, double *latency_us)
@@ -197,9 +544,9 @@ int aidw_request_latency_us(aidw_ctx *ctx, aidw_request id, double *latency_us)
         return AIDW_ERR_NOT_FOUND;
     if (!it->second.done)
         return AIDW_PENDING;
-    *latency_us = std::chrono::duration<double, std::micro>(it->second.t_done -
-                                                            it->second.t_submit)
-                      .count();
+    *latency_us =
+        std::chrono::duration<double, std::micro>(it->second.t_done - it->second.t_submit)
+            .count();
     return AIDW_OK;
 }
 
@@ -217,6 +564,23 @@ int aidw_release_request(aidw_ctx *ctx, aidw_request id)
     if (!it->second.done)
         return AIDW_PENDING;
     rt->reqs.erase(it);
+    return AIDW_OK;
+}
+
+int aidw_serving_get_stats(aidw_ctx *ctx, aidw_serving_stats *out)
+{
+    if (!ctx || !out)
+        return AIDW_ERR_INVALID_ARG;
+    ServingRuntime *rt = ctx_serving(ctx);
+    if (!rt) {
+        std::memset(out, 0, sizeof(*out));
+        return AIDW_OK;
+    }
+    std::lock_guard<std::mutex> g(rt->mu);
+    *out = rt->stats;
+    out->queued = static_cast<int64_t>(rt->queue.size());
+    out->in_flight_bytes = rt->in_flight;
+    out->budget_bytes = rt->budget;
     return AIDW_OK;
 }
 

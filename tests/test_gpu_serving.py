@@ -1,0 +1,174 @@
+"""Serving with continuous batching (aidw_submit / aidw_poll / aidw_wait) on the GPU.
+
+Requests of different datasets and sizes are admitted by device footprint into persistent batch
+launches that overlap on two streams; each result must equal the oracle within tolerance and be
+bit-identical to the same request served alone.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1511_02186_gb300 import aidw, workloads
+from parity import TOL_F32, TOL_F64, oracle_for, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def datasets(ctx, seed, count, n_max=60000):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(64, n_max))
+        wl = workloads.small_case(seed * 100 + i, n, 1, k=10,
+                                  pattern="clustered" if i % 2 else "uniform",
+                                  side=float(rng.uniform(10, 1000)))
+        out.append((wl, ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)))
+    return out
+
+
+def request(wl, seed, m, device):
+    import torch
+    rng = np.random.default_rng(seed)
+    side = np.sqrt(wl.area)
+    qx, qy = rng.uniform(0, side, m), rng.uniform(0, side, m)
+    w = workloads.Workload(wl.name, wl.x, wl.y, wl.z, wl.area, qx, qy, k=wl.k)
+    if device:
+        tq = (torch.as_tensor(qx, dtype=torch.float32, device="cuda"),
+              torch.as_tensor(qy, dtype=torch.float32, device="cuda"))
+        out = torch.full((m,), float("nan"), dtype=torch.float32, device="cuda")
+    else:
+        tq = (qx.astype(np.float32), qy.astype(np.float32))
+        out = np.full(m, np.nan, dtype=np.float32)
+    return w, tq, out
+
+
+def to_np(a):
+    return a.cpu().numpy() if hasattr(a, "cpu") else a
+
+
+def test_served_requests_match_oracle_and_overlap():
+    with aidw.Context(0) as ctx:
+        dss = datasets(ctx, 1, 6)
+        rng = np.random.default_rng(2)
+        reqs = []
+        for i in range(40):
+            wl, ds = dss[int(rng.integers(0, len(dss)))]
+            m = int(rng.integers(1, 6000))
+            w, (qx, qy), out = request(wl, 1000 + i, m, device=bool(i % 2))
+            p = aidw.default_params(k=10)
+            rc, rid = ctx.submit(ds, qx, qy, p, out)
+            assert rc == aidw.OK
+            reqs.append((w, rid, out, (qx, qy)))
+        for w, rid, out, _ in reqs:
+            assert ctx.wait(rid, 60_000_000) == aidw.OK
+        for w, rid, out, _ in reqs:
+            ref, _ = oracle_for(w, aidw.F32C)
+            assert rel_err(to_np(out), ref).max() <= TOL_F32
+            assert ctx.latency_us(rid) > 0
+            assert ctx.release(rid) == aidw.OK
+        st = ctx.serving_stats()
+        assert st.completed == 40 and st.failed == 0
+        assert st.batched_requests == 40
+        assert st.launches < 40, "requests should share launches"
+        assert st.max_concurrent_launches >= 2, "launches should overlap on the device"
+
+
+def test_alone_equals_in_the_mix():
+    import torch
+    with aidw.Context(0) as ctx:
+        dss = datasets(ctx, 3, 4)
+        wl, ds = dss[1]
+        w, (qx, qy), out_alone = request(wl, 77, 4321, device=True)
+        p = aidw.default_params(k=10)
+        rc, rid = ctx.submit(ds, qx, qy, p, out_alone)
+        assert rc == aidw.OK and ctx.wait(rid, 60_000_000) == aidw.OK
+        # The same request again, submitted inside a burst of others.
+        out_mix = torch.full_like(out_alone, float("nan"))
+        ids = []
+        for i in range(12):
+            wl2, ds2 = dss[i % 4]
+            _, (a, b), o = request(wl2, 500 + i, 1000 + 300 * i, device=True)
+            ids.append((ctx.submit(ds2, a, b, p, o)[1], (a, b, o)))
+            if i == 6:
+                rc, mid = ctx.submit(ds, qx, qy, p, out_mix)
+                assert rc == aidw.OK
+        for rid2, _ in ids:
+            assert ctx.wait(rid2, 60_000_000) == aidw.OK
+        assert ctx.wait(mid, 60_000_000) == aidw.OK
+        torch.cuda.synchronize()
+        assert torch.equal(out_alone, out_mix)
+
+
+def test_admission_by_footprint_and_oversize():
+    with aidw.Context(0) as ctx:
+        ctx.serving_configure(inflight_bytes=6 << 20, max_batch_requests=4, streams=2)
+        dss = datasets(ctx, 4, 3, n_max=20000)
+        p = aidw.default_params(k=10)
+        reqs = []
+        for i in range(16):
+            wl, ds = dss[i % 3]
+            w, (qx, qy), out = request(wl, 900 + i, 3000, device=False)
+            rc, rid = ctx.submit(ds, qx, qy, p, out)
+            assert rc == aidw.OK
+            reqs.append((w, rid, out))
+        for w, rid, out in reqs:
+            assert ctx.wait(rid, 60_000_000) == aidw.OK
+            ref, _ = oracle_for(w, aidw.F32C)
+            assert rel_err(out, ref).max() <= TOL_F32
+        st = ctx.serving_stats()
+        assert st.launches >= 4  # at most 4 requests per launch
+        assert st.in_flight_bytes == 0
+        # A request whose footprint alone exceeds the budget fails with OOM, not a hang.
+        wl, ds = dss[0]
+        w, (qx, qy), out = request(wl, 1, 200000, device=False)
+        rc, rid = ctx.submit(ds, qx, qy, p, out)
+        assert rc == aidw.OK
+        assert ctx.wait(rid, 60_000_000) == aidw.ERR_OOM
+
+
+def test_solo_paths_fp64_and_knn():
+    import torch
+    with aidw.Context(0) as ctx:
+        dss = datasets(ctx, 5, 2)
+        wl, ds = dss[0]
+        rng = np.random.default_rng(8)
+        side = np.sqrt(wl.area)
+        qx, qy = rng.uniform(0, side, 700), rng.uniform(0, side, 700)
+        w = workloads.Workload(wl.name, wl.x, wl.y, wl.z, wl.area, qx, qy, k=10)
+        out64 = np.full(700, np.nan)
+        p64 = aidw.default_params(k=10, precision=aidw.F64)
+        rc, r1 = ctx.submit(ds, qx, qy, p64, out64)
+        assert rc == aidw.OK
+        out32 = np.full(700, np.nan, dtype=np.float32)
+        knn = np.full((700, 10), -1, dtype=np.int32)
+        rc, r2 = ctx.submit(ds, qx.astype(np.float32), qy.astype(np.float32),
+                            aidw.default_params(k=10), out32, out_knn=knn)
+        assert rc == aidw.OK
+        assert ctx.wait(r1, 60_000_000) == aidw.OK and ctx.wait(r2, 60_000_000) == aidw.OK
+        ref64, _ = oracle_for(w, aidw.F64)
+        assert rel_err(out64, ref64).max() <= TOL_F64
+        ref32, _ = oracle_for(w, aidw.F32C)
+        assert rel_err(out32, ref32).max() <= TOL_F32
+        assert (knn >= 0).all()
+        rc, done = ctx.poll(r1)
+        assert rc == aidw.OK and done
+        assert ctx.release(r1) == aidw.OK
+        assert ctx.poll(r1)[0] == aidw.ERR_NOT_FOUND
+        del torch
+
+
+def test_submit_rejects_bad_requests():
+    with aidw.Context(0) as ctx:
+        wl = workloads.small_case(9, 50, 5, k=3)
+        ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+        out = np.zeros(5, dtype=np.float32)
+        q = wl.qx.astype(np.float32)
+        assert ctx.submit(ds, q, q, aidw.default_params(k=51), out)[0] == aidw.ERR_INVALID_ARG
+        bad = q.copy()
+        bad[2] = np.nan
+        assert ctx.submit(ds, bad, q, aidw.default_params(k=3), out)[0] == aidw.ERR_INVALID_ARG
+        ds.destroy()
+        assert ctx.submit(ds, q, q, aidw.default_params(k=3), out)[0] in (
+            aidw.ERR_NOT_FOUND, aidw.ERR_INVALID_ARG)
+        time.sleep(0.01)
