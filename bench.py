@@ -198,6 +198,103 @@ def oracle_rate_small(wl, threads):
     return q * wl.n / dt, f"{q} seeded queries x all {wl.n} data points per step", dt
 
 
+# ---- batched and served configurations -------------------------------------------------------
+
+def bench_batched(ctx, steps: int, warmup: int, dev, stream):
+    """256 independent datasets (n log-uniform in [1,024, 262,144], m log-uniform in
+    [1,024, 65,536], side log-uniform in [10, 1000], uniform or clustered, k in {6, 10, 15}) in
+    one persistent launch replayed from a CUDA graph."""
+    import torch
+    from paper_1511_02186_gb300 import aidw, workloads
+    wls = workloads.batched(0)
+    items = []
+    for wl in wls:
+        ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+        qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)
+        qy = torch.as_tensor(wl.qy, dtype=torch.float32, device=dev)
+        out = torch.empty(wl.m, dtype=torch.float32, device=dev)
+        items.append((ds, qx, qy, aidw.default_params(k=wl.k), out, None))
+    pairs = float(sum(wl.n * wl.m for wl in wls))
+    pb = ctx.batch_create(items)
+    for _ in range(max(1, warmup)):
+        pb.launch(stream.cuda_stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        pb.launch(stream.cuda_stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    pb.destroy()
+    for it in items:
+        it[0].destroy()
+    return {"workload": "batched_256_datasets", "datasets": len(wls),
+            "pair_evals_per_launch": pairs, "launches": steps,
+            "ms_per_launch": statistics.mean(ms),
+            "value": pairs / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "queries": int(sum(wl.m for wl in wls)),
+            "launch": "one persistent work-queue kernel per batch, replayed from a CUDA graph"}
+
+
+def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s: float):
+    """64 resident datasets (n log-uniform in [16K, 1M]); Poisson arrivals of requests with
+    256..262,144 query points (log-uniform, host arrays) uniform in the dataset's square.
+    Two runs: a sustainable rate (half the measured capacity) and the nominal 2,000 req/s."""
+    from paper_1511_02186_gb300 import aidw, workloads
+    dsw = workloads.served_datasets(0)
+    handles = [ctx.create_dataset(w.x, w.y, w.z, w.area) for w in dsw]
+    p = aidw.default_params(k=10)
+    results = {}
+    mean_pairs = None
+    for label, rate, window in (("sustained", None, window_s),
+                                ("nominal_2000_per_s", 2000.0, nominal_window_s)):
+        if rate is None:
+            probe = workloads.served_requests(dsw, seed=11, rate=2000.0, duration_s=1.0)
+            mean_pairs = statistics.mean(dsw[d].n * len(qx) for _, d, qx, _ in probe)
+            rate = max(1.0, 0.5 * capacity_pairs_s / mean_pairs)
+        reqs = workloads.served_requests(dsw, seed=12, rate=rate, duration_s=window)
+        prepared = [(t, d, qx.astype(np.float32), qy.astype(np.float32),
+                     np.empty(len(qx), dtype=np.float32)) for t, d, qx, qy in reqs]
+        ids = []
+        again = 0
+        t0 = time.perf_counter()
+        for t, d, qx, qy, out in prepared:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            while True:
+                rc, rid = ctx.submit(handles[d], qx, qy, p, out)
+                if rc == aidw.ERR_AGAIN:
+                    again += 1
+                    time.sleep(0.001)
+                    continue
+                break
+            ids.append((rid, dsw[d].n * len(qx)))
+        for rid, _ in ids:
+            ctx.wait(rid, -1)
+        wall = time.perf_counter() - t0
+        lat = np.array([ctx.latency_us(rid) for rid, _ in ids]) / 1e3
+        for rid, _ in ids:
+            ctx.release(rid)
+        pairs = float(sum(x for _, x in ids))
+        results[label] = {"rate_req_per_s": rate, "window_s": window, "requests": len(ids),
+                          "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99)),
+                          "max_ms": float(lat.max()),
+                          "throughput": pairs / wall, "unit": UNIT,
+                          "offered": rate * mean_pairs, "resubmits_after_again": again}
+    st = ctx.serving_stats()
+    results["launches"] = int(st.launches)
+    results["max_concurrent_launches"] = int(st.max_concurrent_launches)
+    results["mean_requests_per_launch"] = st.batched_requests / max(1, st.launches)
+    results["workload"] = "served_64_datasets_poisson"
+    for h in handles:
+        h.destroy()
+    return results
+
+
 # ---- GPU arm -----------------------------------------------------------------------------------
 
 def run_gpu(args):
@@ -328,6 +425,13 @@ def run_gpu(args):
     h2d = 3 * 8 * wl.n + 2 * 4 * wl.m
     d2h = 4 * wl.m
 
+    batched = bench_batched(ctx, max(2, args.steps), args.warmup, dev, stream)
+    served = None
+    if world == 1 or rank == 0:
+        sctx = aidw.Context(local)
+        served = bench_served(sctx, value / world, 2.0, 0.5)
+        sctx.close()
+
     line = None
     if rank == 0:
         threads = os.cpu_count() or 1
@@ -362,6 +466,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h,
                     "includes": "dataset upload + conversion, query upload, both phases, "
                                 "result download"},
+            "batched": batched,
+            "served": served,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads,
