@@ -22,12 +22,12 @@ inline size_t align256(size_t b)
     return (b + 255) & ~static_cast<size_t>(255);
 }
 
-// Converts caller arrays (float or double) into the four padded device layouts and counts
-// non-finite inputs. Padding points are +inf with value 0.
+// Converts caller arrays (float or double) into unsorted FP32 staging arrays and the padded
+// FP64 layout, and counts non-finite inputs. FP64 padding points are +inf with value 0.
 template <typename T>
 __global__ void convert_dataset_kernel(const T *__restrict__ x, const T *__restrict__ y,
                                        const T *__restrict__ z, int64_t n, int64_t n_pad,
-                                       float4 *nxy2, float2 *zz, double2 *xy64, double *z64,
+                                       float2 *xy32, float *z32, double2 *xy64, double *z64,
                                        unsigned long long *bad)
 {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -40,22 +40,46 @@ __global__ void convert_dataset_kernel(const T *__restrict__ x, const T *__restr
             b = static_cast<double>(y[i]);
             c = static_cast<double>(z[i]);
             nb += (isfinite(a) && isfinite(b) && isfinite(c)) ? 0 : 1;
+            const float fa = static_cast<float>(a), fb = static_cast<float>(b);
+            const float fc = static_cast<float>(c);
+            // FP32 copies must stay finite too (values beyond float range are rejected).
+            if (!(isfinite(fa) && isfinite(fb) && isfinite(fc)))
+                ++nb;
+            xy32[i] = make_float2(fa, fb);
+            z32[i] = fc;
         } else {
             a = b = CUDART_INF;
             c = 0.0;
         }
-        const float fa = static_cast<float>(a), fb = static_cast<float>(b);
-        const float fc = static_cast<float>(c);
-        // FP32 copies must stay finite too (coordinates beyond float range are rejected).
-        if (i < n && !(isfinite(fa) && isfinite(fb) && isfinite(fc)))
-            ++nb;
-        nxy2[i] = make_float4(-fa, -fa, -fb, -fb);
-        zz[i] = make_float2(fc, fc);
         xy64[i] = make_double2(a, b);
         z64[i] = c;
     }
     if (nb)
         atomicAdd(bad, nb);
+}
+
+// Writes the Z-ordered FP32 layout: stored position i holds caller point perm[i] (padding
+// positions, perm[i] >= n, hold +inf points with value 0).
+__global__ void gather_dataset_kernel(const float2 *__restrict__ xy32,
+                                      const float *__restrict__ z32,
+                                      const uint32_t *__restrict__ perm, int64_t n,
+                                      int64_t n_pad, float4 *nxy2, float2 *zz, int32_t *orig)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_pad;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t p = perm[i];
+        if (p < n) {
+            const float2 q = xy32[p];
+            const float v = z32[p];
+            nxy2[i] = make_float4(-q.x, -q.x, -q.y, -q.y);
+            zz[i] = make_float2(v, v);
+            orig[i] = static_cast<int32_t>(p);
+        } else {
+            nxy2[i] = make_float4(-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+            zz[i] = make_float2(0.0f, 0.0f);
+            orig[i] = -1;
+        }
+    }
 }
 
 }  // namespace
@@ -366,6 +390,69 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
     return AIDW_OK;
 }
 
+// Queries below this count keep the plain split scan for phase 1 (ordering them would cost
+// more than it saves).
+constexpr int64_t kCullMinQueries = 2048;
+
+bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m)
+{
+    return precision == AIDW_F32C && ds.n_pad / kTileF32Knn <= kMaxCullTiles &&
+           m >= kCullMinQueries;
+}
+
+size_t culled_extra_bytes(int64_t m)
+{
+    const size_t mm = static_cast<size_t>(m);
+    return 4 * align256(mm * sizeof(uint32_t)) + align256(radix_scratch_bytes(m));
+}
+
+// FP32 interpolation with Z-ordered queries and the pruned phase-1 scan: Morton keys of the
+// queries over the dataset's box, stable radix sort, gather, phase 1 (pruned), selection and
+// finalisation writing back to the caller's order; phase 2 runs on the ordered queries.
+int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
+                   const aidw_params &p, const float *qx, const float *qy, const Scratch &sc,
+                   void *extra, float *out, float *out_alpha, int32_t *out_knn, cudaStream_t st,
+                   bool profile)
+{
+    const AlphaMap am = alpha_map(p);
+    const int64_t m = pl.m;
+    const size_t b4 = align256(static_cast<size_t>(m) * sizeof(uint32_t));
+    char *e = static_cast<char *>(extra);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(e);
+    uint32_t *perm = reinterpret_cast<uint32_t *>(e + b4);
+    float *sqx = reinterpret_cast<float *>(e + 2 * b4);
+    float *sqy = reinterpret_cast<float *>(e + 3 * b4);
+    void *sort_tmp = e + 4 * b4;
+    if (profile)
+        cudaEventRecord(ctx->ev[0], st);
+    bool ok = morton_keys(qx, qy, nullptr, m, m, ds.box, keys, perm, st) == cudaSuccess;
+    ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
+    ok = ok && gather_queries(qx, qy, perm, m, sqx, sqy, st) == cudaSuccess;
+    ok = ok && launch_f32_knn_cull(ds, pl, sqx, sqy, p.k, sc, ctx->d_err, st) == cudaSuccess;
+    if (profile)
+        cudaEventRecord(ctx->ev[1], st);
+    ok = ok && launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
+                   cudaSuccess;
+    if (profile)
+        cudaEventRecord(ctx->ev[2], st);
+    ok = ok && launch_f32_weights(ds, pl, sqx, sqy, sc, ctx->d_err, st) == cudaSuccess;
+    if (profile)
+        cudaEventRecord(ctx->ev[3], st);
+    ok = ok && launch_f32_finalize(pl, sc, out, st, perm) == cudaSuccess;
+    if (!ok)
+        return AIDW_ERR_CUDA;
+    if (profile) {
+        cudaEventRecord(ctx->ev[4], st);
+        ctx->last = aidw_kernel_times{};
+        ctx->last.splits = pl.knn.splits;
+        ctx->last.query_blocks = pl.knn.qblocks;
+        ctx->last.launches = 4 + 14;  // + Morton keys, 12 radix-sort passes, gather
+        ctx->last.weight_splits = pl.w.splits;
+        ctx->last_valid = true;
+    }
+    return AIDW_OK;
+}
+
 // Reads and clears the on-device error word (synchronous).
 int consume_device_error(aidw_ctx *ctx, cudaStream_t st)
 {
@@ -425,9 +512,14 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         }
     }
 
-    const Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
-                              force_knn_splits, force_w_splits);
-    const size_t sb = scratch_bytes(p->precision, pl, p->k);
+    Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
+                        force_knn_splits, force_w_splits);
+    const bool cull = force_knn_splits == 0 && use_culled_knn(p->precision, ds, m);
+    if (cull) {
+        pl.knn.splits = 1;
+        pl.knn.split_len = ds.n_pad;
+    }
+    const size_t sb = scratch_bytes(p->precision, pl, p->k) + (cull ? culled_extra_bytes(m) : 0);
     // Staging for host arrays.
     const size_t b_q = (kq == 0 ? align256(m * es) : 0) + (kqy == 0 ? align256(m * es) : 0);
     const size_t b_o = ko == 0 ? align256(m * es) : 0;
@@ -440,6 +532,7 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         return rc;
     Scratch sc;
     scratch_carve(blk, p->precision, pl, p->k, &sc);
+    void *extra = static_cast<char *>(blk) + scratch_bytes(p->precision, pl, p->k);
     char *stage = static_cast<char *>(blk) + sb;
     const void *dqx = qx, *dqy = qy;
     void *dout = out;
@@ -472,8 +565,11 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         ctx_free(ctx, blk, total, st);
         return AIDW_ERR_CUDA;
     }
-    rc = enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn, st,
-                               ctx->profiling);
+    rc = cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, static_cast<const float *>(dqx),
+                               static_cast<const float *>(dqy), sc, extra,
+                               static_cast<float *>(dout), dalpha, dknn, st, ctx->profiling)
+              : enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn,
+                                      st, ctx->profiling);
     if (rc == AIDW_OK && host_any) {
         ok = true;
         if (ko == 0)
@@ -622,8 +718,11 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     const size_t es = dtype == AIDW_DTYPE_F64 ? sizeof(double) : sizeof(float);
     const int64_t n_pad = (n + kPadPoints - 1) / kPadPoints * kPadPoints;
     const size_t np = static_cast<size_t>(n_pad);
+    const int64_t ntiles = n_pad / kTileF32Knn;
     const size_t bytes = align256(np * sizeof(float4)) + align256(np * sizeof(float2)) +
-                         align256(np * sizeof(double2)) + align256(np * sizeof(double));
+                         align256(np * sizeof(int32_t)) + align256(np * sizeof(double2)) +
+                         align256(np * sizeof(double)) +
+                         align256(ntiles * sizeof(float4)) + align256(sizeof(float4));
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         if (ctx->fail_after >= 0) {
@@ -647,41 +746,65 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
         unreserve();
         return AIDW_ERR_OOM;
     }
-    // Stage host arrays.
-    void *stage = nullptr;
-    const void *sx = x, *sy = y, *sz = z;
+    // Temporary block: host-array staging (if any), unsorted FP32 copies, sort keys and values,
+    // radix-sort scratch, bounding-box scratch.
     const size_t one = align256(static_cast<size_t>(n) * es);
-    int rc = AIDW_OK;
-    if (kx == 0 || ky == 0 || kz == 0) {
-        if (cudaMalloc(&stage, 3 * one) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(blk);
-            unreserve();
-            return AIDW_ERR_OOM;
-        }
-        char *s = static_cast<char *>(stage);
+    const bool stage_host = kx == 0 || ky == 0 || kz == 0;
+    const size_t tmp_bytes = (stage_host ? 3 * one : 0) + align256(np * sizeof(float2)) +
+                             align256(np * sizeof(float)) + 2 * align256(np * sizeof(uint32_t)) +
+                             align256(radix_scratch_bytes(n_pad)) + 256;
+    void *tmp = nullptr;
+    if (cudaMalloc(&tmp, tmp_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(blk);
+        unreserve();
+        return AIDW_ERR_OOM;
+    }
+    char *t = static_cast<char *>(tmp);
+    const void *sx = x, *sy = y, *sz = z;
+    if (stage_host) {
         if (kx == 0) {
-            cudaMemcpy(s, x, n * es, cudaMemcpyHostToDevice);
-            sx = s;
+            cudaMemcpy(t, x, n * es, cudaMemcpyHostToDevice);
+            sx = t;
         }
         if (ky == 0) {
-            cudaMemcpy(s + one, y, n * es, cudaMemcpyHostToDevice);
-            sy = s + one;
+            cudaMemcpy(t + one, y, n * es, cudaMemcpyHostToDevice);
+            sy = t + one;
         }
         if (kz == 0) {
-            cudaMemcpy(s + 2 * one, z, n * es, cudaMemcpyHostToDevice);
-            sz = s + 2 * one;
+            cudaMemcpy(t + 2 * one, z, n * es, cudaMemcpyHostToDevice);
+            sz = t + 2 * one;
         }
+        t += 3 * one;
     }
-    DatasetRec rec;
+    float2 *xy32 = reinterpret_cast<float2 *>(t);
+    t += align256(np * sizeof(float2));
+    float *z32 = reinterpret_cast<float *>(t);
+    t += align256(np * sizeof(float));
+    uint32_t *keys = reinterpret_cast<uint32_t *>(t);
+    t += align256(np * sizeof(uint32_t));
+    uint32_t *perm = reinterpret_cast<uint32_t *>(t);
+    t += align256(np * sizeof(uint32_t));
+    void *sort_tmp = t;
+    t += align256(radix_scratch_bytes(n_pad));
+    uint32_t *box_scratch = reinterpret_cast<uint32_t *>(t);
+
     char *b = static_cast<char *>(blk);
     float4 *nxy2 = reinterpret_cast<float4 *>(b);
     b += align256(np * sizeof(float4));
     float2 *zz = reinterpret_cast<float2 *>(b);
     b += align256(np * sizeof(float2));
+    int32_t *orig = reinterpret_cast<int32_t *>(b);
+    b += align256(np * sizeof(int32_t));
     double2 *xy64 = reinterpret_cast<double2 *>(b);
     b += align256(np * sizeof(double2));
     double *z64 = reinterpret_cast<double *>(b);
+    b += align256(np * sizeof(double));
+    float4 *tbox = reinterpret_cast<float4 *>(b);
+    b += align256(ntiles * sizeof(float4));
+    float4 *box = reinterpret_cast<float4 *>(b);
+
+    int rc = AIDW_OK;
     cudaMemset(ctx->d_bad, 0, sizeof(unsigned long long));
     const int threads = 256;
     const int blocks = static_cast<int>(std::min<int64_t>((n_pad + threads - 1) / threads,
@@ -689,26 +812,46 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     if (dtype == AIDW_DTYPE_F64)
         convert_dataset_kernel<double><<<blocks, threads>>>(
             static_cast<const double *>(sx), static_cast<const double *>(sy),
-            static_cast<const double *>(sz), n, n_pad, nxy2, zz, xy64, z64, ctx->d_bad);
+            static_cast<const double *>(sz), n, n_pad, xy32, z32, xy64, z64, ctx->d_bad);
     else
         convert_dataset_kernel<float><<<blocks, threads>>>(
             static_cast<const float *>(sx), static_cast<const float *>(sy),
-            static_cast<const float *>(sz), n, n_pad, nxy2, zz, xy64, z64, ctx->d_bad);
+            static_cast<const float *>(sz), n, n_pad, xy32, z32, xy64, z64, ctx->d_bad);
     unsigned long long bad = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpy(&bad, ctx->d_bad, sizeof(bad), cudaMemcpyDeviceToHost) != cudaSuccess)
         rc = AIDW_ERR_CUDA;
     else if (bad)
         rc = AIDW_ERR_INVALID_ARG;
-    if (stage)
-        cudaFree(stage);
+    // Z-order the FP32 copy and box every tile.
+    if (rc == AIDW_OK) {
+        bool ok = bbox_of(xy32, n, box_scratch, box, 0) == cudaSuccess;
+        ok = ok && morton_keys(nullptr, nullptr, xy32, n, n_pad, box, keys, perm, 0) ==
+                       cudaSuccess;
+        ok = ok && radix_sort_pairs(keys, perm, n_pad, sort_tmp, 0) == cudaSuccess;
+        if (ok) {
+            gather_dataset_kernel<<<blocks, threads>>>(xy32, z32, perm, n, n_pad, nxy2, zz, orig);
+            ok = cudaGetLastError() == cudaSuccess;
+        }
+        ok = ok && tile_boxes(nxy2, ntiles, tbox, 0) == cudaSuccess;
+        ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            rc = AIDW_ERR_CUDA;
+        }
+    }
+    cudaFree(tmp);
     if (rc) {
         cudaFree(blk);
         unreserve();
         return rc;
     }
+    DatasetRec rec;
     rec.dev.nxy2 = nxy2;
     rec.dev.zz = zz;
+    rec.dev.orig = orig;
+    rec.dev.tile_box = tbox;
+    rec.dev.box = box;
     rec.dev.xy64 = xy64;
     rec.dev.z64 = z64;
     rec.dev.n = n;

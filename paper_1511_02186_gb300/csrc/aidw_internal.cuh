@@ -44,12 +44,17 @@ struct AlphaMap {
 
 // FP32 copies are stored negated and duplicated, (-x, -x, -y, -y) and (z, z), so that one
 // shared-memory load yields the register pairs that packed FP32x2 instructions operate on for
-// two queries at once (q + (-x) is exactly q - x).
+// two queries at once (q + (-x) is exactly q - x). They are kept in Z-order (Morton order of
+// the points), with orig[] mapping a stored position back to the caller's index and one
+// bounding box per 512-point tile. The FP64 copies keep the caller's order.
 struct DatasetDev {
-    const float4 *nxy2;   // [n_pad] (-x, -x, -y, -y)
-    const float2 *zz;     // [n_pad] (z, z)
-    const double2 *xy64;  // [n_pad]
-    const double *z64;    // [n_pad]
+    const float4 *nxy2;     // [n_pad] (-x, -x, -y, -y), Z-order
+    const float2 *zz;       // [n_pad] (z, z), Z-order
+    const int32_t *orig;    // [n_pad] caller's index of each stored point, -1 for padding
+    const float4 *tile_box; // [n_pad / kTileF32Knn] (xmin, ymin, xmax, ymax) of finite points
+    const float4 *box;      // [1] bounding box of all points
+    const double2 *xy64;    // [n_pad] caller's order
+    const double *z64;      // [n_pad] caller's order
     int64_t n;
     int64_t n_pad;
 };
@@ -100,11 +105,30 @@ cudaError_t launch_f32_knn(const DatasetDev &ds, const Plan &pl, const float *qx
                            cudaStream_t st);
 cudaError_t launch_f32_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
-                              cudaStream_t st);
+                              cudaStream_t st, const uint32_t *perm = nullptr);
 cudaError_t launch_f32_weights(const DatasetDev &ds, const Plan &pl, const float *qx,
                                const float *qy, const Scratch &sc, int *err, cudaStream_t st);
 cudaError_t launch_f32_finalize(const Plan &pl, const Scratch &sc, float *out,
+                                cudaStream_t st, const uint32_t *perm = nullptr);
+// Phase 1 over Z-ordered queries with nearest-first tile visiting and bounding-box pruning
+// (one split); sqx / sqy are the queries in Z-order.
+constexpr int64_t kMaxCullTiles = 8192;
+cudaError_t launch_f32_knn_cull(const DatasetDev &ds, const Plan &pl, const float *sqx,
+                                const float *sqy, int k, const Scratch &sc, int *err,
                                 cudaStream_t st);
+
+// Spatial helpers (spatial.cu).
+size_t radix_scratch_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tmp,
+                             cudaStream_t st);
+cudaError_t bbox_of(const float2 *xy, int64_t n, uint32_t *scratch4, float4 *box,
+                    cudaStream_t st);
+cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_t n,
+                        int64_t n_total, const float4 *box, uint32_t *keys, uint32_t *vals,
+                        cudaStream_t st);
+cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st);
+cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
+                           float *sqx, float *sqy, cudaStream_t st);
 
 cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *qx,
                            const double *qy, int k, const Scratch &sc, int *err,

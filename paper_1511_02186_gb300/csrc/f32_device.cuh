@@ -85,6 +85,68 @@ __device__ __forceinline__ void drain(TileSeq &ts, int t, int ntiles)
     }
 }
 
+// One tile of kTileF32Knn points (stored positions pbase..) through the phase-1 filter and,
+// where a sign bit fires, the exact insertion (see knn_unit).
+template <int KP, int Q, bool IDX>
+__device__ __forceinline__ void knn_tile(const float4 *tb, int64_t pbase, float2 (&qxp)[Q / 2],
+                                         float2 (&qyp)[Q / 2], float2 (&nthr)[Q / 2],
+                                         float (&L)[Q][KP], int32_t *idx_smem)
+{
+    constexpr int H = Q / 2;
+    const int tid = threadIdx.x;
+    for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
+        uint32_t acc[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            acc[j] = 0u;
+#pragma unroll
+        for (int u = 0; u < kChunkKnn; u += 2) {
+            const float4 pa = tb[c + u];
+            const float4 pb = tb[c + u + 1];
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float2 dxa = __fadd2_rn(qxp[h], make_float2(pa.x, pa.y));
+                const float2 dya = __fadd2_rn(qyp[h], make_float2(pa.z, pa.w));
+                const float2 va = __ffma2_rn(dxa, dxa, __ffma2_rn(dya, dya, nthr[h]));
+                const float2 dxb = __fadd2_rn(qxp[h], make_float2(pb.x, pb.y));
+                const float2 dyb = __fadd2_rn(qyp[h], make_float2(pb.z, pb.w));
+                const float2 vb = __ffma2_rn(dxb, dxb, __ffma2_rn(dyb, dyb, nthr[h]));
+                acc[2 * h] = sign_or3(acc[2 * h], va.x, vb.x);
+                acc[2 * h + 1] = sign_or3(acc[2 * h + 1], va.y, vb.y);
+            }
+        }
+        uint32_t any = 0u;
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            any |= acc[j];
+        if (static_cast<int32_t>(any) < 0) {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (static_cast<int32_t>(acc[j]) < 0) {
+                    const float qxj = (j & 1) ? qxp[j / 2].y : qxp[j / 2].x;
+                    const float qyj = (j & 1) ? qyp[j / 2].y : qyp[j / 2].x;
+#pragma unroll 1
+                    for (int u = 0; u < kChunkKnn; ++u) {
+                        const float4 p = tb[c + u];
+                        const float d = dist2_neg(qxj, qyj, p.x, p.z);
+                        if (d < L[j][KP - 1]) {
+                            if (IDX)
+                                index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
+                                                 d, static_cast<int32_t>(pbase + c + u));
+                            list_insert<KP>(L[j], d);
+                        }
+                    }
+                    const float nt = neg_filter_threshold(L[j][KP - 1]);
+                    if (j & 1)
+                        nthr[j / 2].y = nt;
+                    else
+                        nthr[j / 2].x = nt;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Phase 1 unit: neighbour lists of Q * kThreads queries over data points [p_begin, p_end).
 //
@@ -160,59 +222,8 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
             ts.seq += ntiles;
             return false;
         }
-        const float4 *tb = tile[b];
         const int64_t pbase = p_begin + static_cast<int64_t>(t) * kTileF32Knn;
-        for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
-            uint32_t acc[Q];
-#pragma unroll
-            for (int j = 0; j < Q; ++j)
-                acc[j] = 0u;
-#pragma unroll
-            for (int u = 0; u < kChunkKnn; u += 2) {
-                const float4 pa = tb[c + u];
-                const float4 pb = tb[c + u + 1];
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const float2 dxa = __fadd2_rn(qxp[h], make_float2(pa.x, pa.y));
-                    const float2 dya = __fadd2_rn(qyp[h], make_float2(pa.z, pa.w));
-                    const float2 va = __ffma2_rn(dxa, dxa, __ffma2_rn(dya, dya, nthr[h]));
-                    const float2 dxb = __fadd2_rn(qxp[h], make_float2(pb.x, pb.y));
-                    const float2 dyb = __fadd2_rn(qyp[h], make_float2(pb.z, pb.w));
-                    const float2 vb = __ffma2_rn(dxb, dxb, __ffma2_rn(dyb, dyb, nthr[h]));
-                    acc[2 * h] = sign_or3(acc[2 * h], va.x, vb.x);
-                    acc[2 * h + 1] = sign_or3(acc[2 * h + 1], va.y, vb.y);
-                }
-            }
-            uint32_t any = 0u;
-#pragma unroll
-            for (int j = 0; j < Q; ++j)
-                any |= acc[j];
-            if (static_cast<int32_t>(any) < 0) {
-#pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    if (static_cast<int32_t>(acc[j]) < 0) {
-                        const float qxj = (j & 1) ? qxp[j / 2].y : qxp[j / 2].x;
-                        const float qyj = (j & 1) ? qyp[j / 2].y : qyp[j / 2].x;
-#pragma unroll 1
-                        for (int u = 0; u < kChunkKnn; ++u) {
-                            const float4 p = tb[c + u];
-                            const float d = dist2_neg(qxj, qyj, p.x, p.z);
-                            if (d < L[j][KP - 1]) {
-                                if (IDX)
-                                    index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
-                                                     d, static_cast<int32_t>(pbase + c + u));
-                                list_insert<KP>(L[j], d);
-                            }
-                        }
-                        const float nt = neg_filter_threshold(L[j][KP - 1]);
-                        if (j & 1)
-                            nthr[j / 2].y = nt;
-                        else
-                            nthr[j / 2].x = nt;
-                    }
-                }
-            }
-        }
+        knn_tile<KP, Q, IDX>(tile[b], pbase, qxp, qyp, nthr, L, idx_smem);
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) {
             fence_proxy_async_smem();
@@ -233,8 +244,10 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
             if (r >= 0) {
                 const int64_t o = (static_cast<int64_t>(s) * k + r) * m + q;
                 part_d2[o] = L[j][i];
-                if (IDX)
-                    part_idx[o] = idx_smem[(j * KP + i) * kThreads + tid];
+                if (IDX) {
+                    const int32_t v = idx_smem[(j * KP + i) * kThreads + tid];
+                    part_idx[o] = v >= 0 ? ds.orig[v] : -1;
+                }
             }
         }
     }
@@ -250,8 +263,10 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
 __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k, double r_exp,
                                              const AlphaMap &am, const float *part_d2,
                                              const int32_t *part_idx, QParamF32 *qp,
-                                             float *out_alpha, int32_t *out_knn)
+                                             float *out_alpha, int32_t *out_knn,
+                                             const uint32_t *perm = nullptr)
 {
+    const int64_t qo = perm ? static_cast<int64_t>(perm[q]) : q;  // caller's query index
     int cur[kMaxSplits];
     float hd[kMaxSplits];
     int32_t hi[kMaxSplits];
@@ -269,7 +284,7 @@ __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k,
                 bs = s;
         d[r] = hd[bs];
         if (out_knn)
-            out_knn[q * k + r] = hi[bs];
+            out_knn[qo * k + r] = hi[bs];
         if (++cur[bs] < k) {
             const int64_t o = (static_cast<int64_t>(bs) * k + cur[bs]) * m + q;
             hd[bs] = __ldcg(part_d2 + o);
@@ -305,7 +320,7 @@ __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k,
     }
     qp[q] = o;
     if (out_alpha)
-        out_alpha[q] = static_cast<float>(alpha);
+        out_alpha[qo] = static_cast<float>(alpha);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -1,0 +1,315 @@
+// Spatial ordering helpers: Morton (Z-order) keys, a stable LSD radix sort of (key, value)
+// pairs, gathers, bounding boxes.
+//
+// Data points are stored in Z-order so that each 512-point tile covers a compact region with a
+// tight bounding box, and every call orders its queries the same way so that each query block
+// is compact too. The phase-1 scan can then visit data tiles nearest-first and skip every tile
+// whose box is provably farther than all of the block's current k-th neighbours. The order
+// changes which tiles are read, never the result: the neighbour lists are exact.
+#include <math_constants.h>
+
+#include <cstdint>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per block and pass
+
+// Spreads the low 16 bits of v to the even bit positions.
+__device__ __forceinline__ uint32_t spread16(uint32_t v)
+{
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t morton_of(float x, float y, float4 box)
+{
+    // 16-bit cells over the box; values outside (or NaN) clamp to the edges.
+    const float sx = box.z > box.x ? 65535.0f / (box.z - box.x) : 0.0f;
+    const float sy = box.w > box.y ? 65535.0f / (box.w - box.y) : 0.0f;
+    const float fx = fminf(fmaxf((x - box.x) * sx, 0.0f), 65535.0f);
+    const float fy = fminf(fmaxf((y - box.y) * sy, 0.0f), 65535.0f);
+    return (spread16(static_cast<uint32_t>(fy)) << 1) | spread16(static_cast<uint32_t>(fx));
+}
+
+// Order-preserving map of floats to unsigned integers (for atomic min / max).
+__device__ __forceinline__ uint32_t f2ord(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float ord2f(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void bbox_kernel(const float2 *__restrict__ xy, int64_t n, uint32_t *ord4)
+{
+    float x0 = CUDART_INF_F, y0 = CUDART_INF_F, x1 = -CUDART_INF_F, y1 = -CUDART_INF_F;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float2 p = xy[i];
+        x0 = fminf(x0, p.x);
+        y0 = fminf(y0, p.y);
+        x1 = fmaxf(x1, p.x);
+        y1 = fmaxf(y1, p.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ord4[0], f2ord(x0));
+        atomicMin(&ord4[1], f2ord(y0));
+        atomicMax(&ord4[2], f2ord(x1));
+        atomicMax(&ord4[3], f2ord(y1));
+    }
+}
+
+__global__ void bbox_finish_kernel(const uint32_t *ord4, float4 *box)
+{
+    *box = make_float4(ord2f(ord4[0]), ord2f(ord4[1]), ord2f(ord4[2]), ord2f(ord4[3]));
+}
+
+// Keys for points (x, y) given as separate float arrays or interleaved pairs; padding slots
+// [n, n_total) get the largest key so they sort last.
+__global__ void morton_keys_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                   const float2 *__restrict__ xy, int64_t n, int64_t n_total,
+                                   const float4 *__restrict__ box, uint32_t *keys,
+                                   uint32_t *vals)
+{
+    const float4 b = *box;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t key = 0xffffffffu;
+        if (i < n) {
+            const float px = xy ? xy[i].x : x[i];
+            const float py = xy ? xy[i].y : y[i];
+            key = morton_of(px, py, b);
+        }
+        keys[i] = key;
+        vals[i] = static_cast<uint32_t>(i);
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *counts,
+                  int nblocks)
+{
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x;
+    h[tid] = 0;
+    __syncthreads();
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j * kSortThreads + tid;
+        if (i < n)
+            atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[static_cast<int64_t>(tid) * nblocks + blockIdx.x] = h[tid];
+}
+
+// Exclusive scan of counts[0..total) in place, by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *counts, int64_t total)
+{
+    __shared__ uint32_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (total + 1023) / 1024;
+    const int64_t b = tid * per, e = min(b + per, total);
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i)
+        s += counts[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = tid >= off ? part[tid - off] : 0u;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[tid] - s;
+    for (int64_t i = b; i < e; ++i) {
+        const uint32_t c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+// Stable scatter: keys of one block keep their input order within each digit.
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                     uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                     int shift, const uint32_t *__restrict__ offsets, int nblocks)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t base_off[256];
+    __shared__ uint32_t running[256];
+    __shared__ uint32_t wcount[W][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base_off[tid] = offsets[static_cast<int64_t>(tid) * nblocks + blockIdx.x];
+    running[tid] = 0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+    for (int j = 0; j < kSortItems; ++j) {
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            wcount[w][tid] = 0;
+        __syncthreads();
+        const int64_t i = base + j * kSortThreads + tid;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t tag = valid ? d : (256u + lane);  // invalid lanes match nobody
+        const uint32_t same = __match_any_sync(0xffffffffu, tag);
+        const uint32_t rank = __popc(same & lt_mask);
+        if (valid && lane == __ffs(same) - 1)
+            wcount[warp][d] = __popc(same);
+        __syncthreads();
+        if (valid) {
+            uint32_t prior = 0;
+            for (int w = 0; w < warp; ++w)
+                prior += wcount[w][d];
+            const uint32_t pos = base_off[d] + running[d] + prior + rank;
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+        uint32_t add = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            add += wcount[w][tid];
+        running[tid] += add;
+        __syncthreads();
+    }
+}
+
+// One warp per tile of kTileF32Knn sorted points: box of the finite points.
+__global__ void tile_box_kernel(const float4 *__restrict__ nxy2, int64_t ntiles, float4 *boxes)
+{
+    const int64_t t = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles)
+        return;
+    float x0 = CUDART_INF_F, y0 = CUDART_INF_F, x1 = -CUDART_INF_F, y1 = -CUDART_INF_F;
+    for (int u = lane; u < kTileF32Knn; u += 32) {
+        const float4 p = nxy2[t * kTileF32Knn + u];
+        const float px = -p.x, py = -p.z;
+        if (isfinite(px) && isfinite(py)) {
+            x0 = fminf(x0, px);
+            y0 = fminf(y0, py);
+            x1 = fmaxf(x1, px);
+            y1 = fmaxf(y1, py);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (lane == 0)
+        boxes[t] = make_float4(x0, y0, x1, y1);
+}
+
+__global__ void gather_pairs_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                    const uint32_t *__restrict__ perm, int64_t m, float *sx,
+                                    float *sy)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t p = perm[i];
+        sx[i] = x[p];
+        sy[i] = y[p];
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int cap)
+{
+    const int64_t b = (n + threads - 1) / threads;
+    return static_cast<unsigned>(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+size_t radix_scratch_bytes(int64_t n)
+{
+    const int64_t nblocks = (n + kSortTile - 1) / kSortTile;
+    return sizeof(uint32_t) * (2 * static_cast<size_t>(n) + 256 * static_cast<size_t>(nblocks));
+}
+
+// Sorts (keys, vals)[0..n) by key, stably; tmp holds radix_scratch_bytes(n) bytes.
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tmp,
+                             cudaStream_t st)
+{
+    if (n <= 1)
+        return cudaSuccess;
+    const int nblocks = static_cast<int>((n + kSortTile - 1) / kSortTile);
+    uint32_t *k2 = static_cast<uint32_t *>(tmp);
+    uint32_t *v2 = k2 + n;
+    uint32_t *counts = v2 + n;
+    uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
+    for (int shift = 0; shift < 32; shift += 8) {
+        radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, n, shift, counts, nblocks);
+        radix_scan_kernel<<<1, 1024, 0, st>>>(counts, static_cast<int64_t>(nblocks) * 256);
+        radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts,
+                                                               nblocks);
+        uint32_t *t = ka;
+        ka = kb;
+        kb = t;
+        t = va;
+        va = vb;
+        vb = t;
+    }
+    return cudaGetLastError();  // four passes: the result is back in keys / vals
+}
+
+// Bounding box of n points of an interleaved array into *box (device), using 16 bytes of
+// scratch.
+cudaError_t bbox_of(const float2 *xy, int64_t n, uint32_t *scratch4, float4 *box,
+                    cudaStream_t st)
+{
+    const uint32_t init[4] = {0xffffffffu, 0xffffffffu, 0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(scratch4, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return e;
+    bbox_kernel<<<grid_for(n, 256, 1024), 256, 0, st>>>(xy, n, scratch4);
+    bbox_finish_kernel<<<1, 1, 0, st>>>(scratch4, box);
+    return cudaGetLastError();
+}
+
+cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_t n,
+                        int64_t n_total, const float4 *box, uint32_t *keys, uint32_t *vals,
+                        cudaStream_t st)
+{
+    morton_keys_kernel<<<grid_for(n_total, 256, 4096), 256, 0, st>>>(x, y, xy, n, n_total, box,
+                                                                     keys, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st)
+{
+    tile_box_kernel<<<grid_for(ntiles * 32, 256, 1 << 20), 256, 0, st>>>(nxy2, ntiles, boxes);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
+                           float *sqx, float *sqy, cudaStream_t st)
+{
+    gather_pairs_kernel<<<grid_for(m, 256, 4096), 256, 0, st>>>(qx, qy, perm, m, sqx, sqy);
+    return cudaGetLastError();
+}
+
+}  // namespace aidw
