@@ -120,7 +120,7 @@ cudaError_t launch_f32_knn_cull(const DatasetDev &ds, const Plan &pl, const floa
 // Spatial helpers (spatial.cu).
 size_t radix_scratch_bytes(int64_t n);
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tmp,
-                             cudaStream_t st);
+                             cudaStream_t st, int bits = 32);
 cudaError_t bbox_of(const float2 *xy, int64_t n, uint32_t *scratch4, float4 *box,
                     cudaStream_t st);
 cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_t n,
@@ -255,6 +255,28 @@ __device__ __forceinline__ double alpha_eq6(double mu, const AlphaMap &am)
     seg = seg < 0 ? 0 : (seg > 3 ? 3 : seg);
     const double t = (mu - (0.1 + 0.2 * seg)) * 5.0;
     return am.level[seg] * (1.0 - t) + am.level[seg + 1] * t;
+}
+
+// Spreads the low 16 bits of v to the even bit positions.
+__device__ __forceinline__ uint32_t spread16(uint32_t v)
+{
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// Z-order (Morton) key of (x, y) on a 65536 x 65536 grid over `box` (xmin, ymin, xmax, ymax);
+// points outside the box, or NaN, clamp to its edges.
+__device__ __forceinline__ uint32_t morton_of(float x, float y, float4 box)
+{
+    const float sx = box.z > box.x ? 65535.0f / (box.z - box.x) : 0.0f;
+    const float sy = box.w > box.y ? 65535.0f / (box.w - box.y) : 0.0f;
+    const float fx = fminf(fmaxf((x - box.x) * sx, 0.0f), 65535.0f);
+    const float fy = fminf(fmaxf((y - box.y) * sy, 0.0f), 65535.0f);
+    return (spread16(static_cast<uint32_t>(fy)) << 1) | spread16(static_cast<uint32_t>(fx));
 }
 
 // Kahan step: adds v to the running sum h whose compensation (excess added so far) is c.

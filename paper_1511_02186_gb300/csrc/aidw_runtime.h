@@ -53,6 +53,13 @@ struct BatchState {
     int n_units = 0;
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
+    // Batch-wide query ordering (Z-order within each item).
+    int32_t count = 0;
+    int64_t total_q = 0, max_m = 0;
+    size_t dyn_smem = 0;
+    uint32_t *keys = nullptr, *vals = nullptr, *item_of = nullptr, *perm = nullptr;
+    float *sqx = nullptr, *sqy = nullptr;
+    void *sort_tmp = nullptr;
 };
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
                 BatchState *bs);

@@ -3,13 +3,17 @@
 //
 // Every item is cut into units that depend only on the item itself (never on what else is in
 // the batch), so an item's result is bit-identical whether it runs alone or in any mix:
-//   KNN     (item, query block, split)  phase-1 scan of one data split       (no wait)
+//   KNN     (item, query block)         pruned phase-1 scan of Z-ordered      (no wait)
+//                                       queries (nearest data tiles first)
 //   SELECT  (item, query block)         merge + Eq. 2-6 for 512 queries      waits for the
 //                                                                            block's KNN splits
 //   WEIGHTS (item, query block, split)  phase-2 scan of one data split       waits for all of
 //                                                                            the item's SELECTs
 //   FINAL   (item, query block)         split merge + Eq. 1 ratio            waits for the
 //                                                                            block's WEIGHTS
+// Before the persistent kernel, the queries of all items are put in Z-order item by item (Morton
+// keys over each item's dataset box, a stable radix sort by key, then a stable sort by item) so
+// that each KNN unit's block is compact; results go back to the caller's order.
 // The work list holds all KNN units, then all SELECT, WEIGHTS and FINAL units, each phase in
 // decreasing item size; CTAs take units in list order from one atomic counter. A unit only
 // waits on units earlier in the list, which running CTAs have already taken and never block
@@ -50,7 +54,11 @@ struct BatchItemDev {
     float *part_d2;
     QParamF32 *qparam;
     float *part_sum;
-    uint32_t *cnt_knn;  // [knn.qblocks] finished phase-1 splits per query block
+    const float *sqx, *sqy;  // the item's queries in Z-order
+    const uint32_t *perm;    // Z-order position -> caller's query index
+    int64_t qoff;            // offset of the item in the batch-wide query arrays
+    int32_t ntiles, ntiles_p2;
+    uint32_t *cnt_knn;  // [knn.qblocks] finished phase-1 units per query block
     uint32_t *cnt_sel;  // [1] finished SELECT units
     uint32_t *cnt_w;    // [w.qblocks] finished phase-2 splits per query block
 };
@@ -99,6 +107,8 @@ __global__ void __launch_bounds__(kThreads, 4)
 f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restrict__ units,
                  int n_units, uint32_t *next, int *err)
 {
+    extern __shared__ unsigned long long order[];  // tile order of a KNN unit
+    __shared__ CullShared cs;
     __shared__ __align__(128) float4 ktile[2][kTileF32Knn];
     __shared__ __align__(128) float4 txy[2][kTileF32W];
     __shared__ __align__(128) float2 tz[2][kTileF32W];
@@ -119,30 +129,57 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
         const WorkUnit wu = units[u];
         const BatchItemDev &it = items[wu.item];
         bool ok = true;
-        if (wu.type == kUnitKnn) {
+        if (wu.type == kUnitKnn && it.ntiles_p2 == 0) {
+            // Dataset too large for the shared-memory tile order: split scan.
             const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.knn.q_per_block;
             const int64_t p0 = static_cast<int64_t>(wu.split) * it.knn.split_len;
             const int64_t p1 = min(p0 + it.knn.split_len, it.ds.n_pad);
             switch (it.kp) {
             case 8:
-                ok = knn_unit<8, 4, false>(it.ds, it.m, qbase, p0, p1, it.qx, it.qy, it.k,
+                ok = knn_unit<8, 4, false>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.k,
                                            wu.split, it.part_d2, nullptr, err, ktile, ts,
                                            nullptr);
                 break;
             case 12:
-                ok = knn_unit<12, 4, false>(it.ds, it.m, qbase, p0, p1, it.qx, it.qy, it.k,
+                ok = knn_unit<12, 4, false>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.k,
                                             wu.split, it.part_d2, nullptr, err, ktile, ts,
                                             nullptr);
                 break;
             case 16:
-                ok = knn_unit<16, 4, false>(it.ds, it.m, qbase, p0, p1, it.qx, it.qy, it.k,
+                ok = knn_unit<16, 4, false>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.k,
                                             wu.split, it.part_d2, nullptr, err, ktile, ts,
                                             nullptr);
                 break;
             default:
-                ok = knn_unit<32, 2, false>(it.ds, it.m, qbase, p0, p1, it.qx, it.qy, it.k,
+                ok = knn_unit<32, 2, false>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.k,
                                             wu.split, it.part_d2, nullptr, err, ktile, ts,
                                             nullptr);
+                break;
+            }
+            if (ok)
+                cta_publish(&it.cnt_knn[wu.qblock]);
+        } else if (wu.type == kUnitKnn) {
+            const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.knn.q_per_block;
+            switch (it.kp) {
+            case 8:
+                ok = knn_cull_unit<8, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
+                                                it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
+                                                ktile, ts, order, nullptr, cs);
+                break;
+            case 12:
+                ok = knn_cull_unit<12, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
+                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
+                                                 ktile, ts, order, nullptr, cs);
+                break;
+            case 16:
+                ok = knn_cull_unit<16, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
+                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
+                                                 ktile, ts, order, nullptr, cs);
+                break;
+            default:
+                ok = knn_cull_unit<32, 2, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
+                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
+                                                 ktile, ts, order, nullptr, cs);
                 break;
             }
             if (ok)
@@ -154,7 +191,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 const int64_t qend = min(qbase + it.knn.q_per_block, it.m);
                 for (int64_t q = qbase + tid; q < qend; q += kThreads)
                     select_query(q, it.m, it.knn.splits, it.k, it.r_exp, it.am, it.part_d2,
-                                 nullptr, it.qparam, it.out_alpha, nullptr);
+                                 nullptr, it.qparam, it.out_alpha, nullptr, it.perm);
                 cta_publish(it.cnt_sel);
             }
         } else if (wu.type == kUnitWeights) {
@@ -163,7 +200,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.w.q_per_block;
                 const int64_t p0 = static_cast<int64_t>(wu.split) * it.w.split_len;
                 const int64_t p1 = min(p0 + it.w.split_len, it.ds.n_pad);
-                ok = weights_unit<kQW32>(it.ds, it.m, qbase, p0, p1, it.qx, it.qy, it.qparam,
+                ok = weights_unit<kQW32>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.qparam,
                                          wu.split, it.part_sum, err, txy, tz, ts);
                 if (ok)
                     cta_publish(&it.cnt_w[wu.qblock]);
@@ -174,7 +211,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.w.q_per_block;
                 const int64_t qend = min(qbase + it.w.q_per_block, it.m);
                 for (int64_t q = qbase + tid; q < qend; q += kThreads)
-                    it.out[q] = finalize_query(q, it.m, it.w.splits, it.part_sum);
+                    it.out[it.perm[q]] = finalize_query(q, it.m, it.w.splits, it.part_sum);
             }
         }
         if (!ok) {
@@ -182,6 +219,50 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 atomicOr(err, kErrTimeout);
             break;
         }
+    }
+}
+
+// Batch-wide query ordering, step 1: Morton key of every query over its item's dataset box;
+// values are batch-wide positions, and the item of every position is recorded.
+__global__ void batch_keys_kernel(const BatchItemDev *__restrict__ items, uint32_t *keys,
+                                  uint32_t *vals, uint32_t *item_of)
+{
+    const BatchItemDev &it = items[blockIdx.y];
+    const float4 box = *it.ds.box;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < it.m;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t g = it.qoff + q;
+        keys[g] = morton_of(it.qx[q], it.qy[q], box);
+        vals[g] = static_cast<uint32_t>(g);
+        item_of[g] = blockIdx.y;
+    }
+}
+
+// Step 2 (after the sort by key): the item of each sorted entry, as the key of a second,
+// stable sort that groups the items while keeping each item's Z-order.
+__global__ void batch_item_keys_kernel(const uint32_t *__restrict__ vals,
+                                       const uint32_t *__restrict__ item_of, int64_t total,
+                                       uint32_t *keys)
+{
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < total;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        keys[j] = item_of[vals[j]];
+}
+
+// Step 3: ordered coordinates and the caller's index of every ordered query.
+__global__ void batch_gather_kernel(const BatchItemDev *__restrict__ items,
+                                    const uint32_t *__restrict__ vals,
+                                    const uint32_t *__restrict__ item_of, int64_t total,
+                                    float *sqx, float *sqy, uint32_t *perm)
+{
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < total;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t g = vals[j];
+        const BatchItemDev &it = items[item_of[g]];
+        const int64_t q = static_cast<int64_t>(g) - it.qoff;
+        sqx[j] = it.qx[q];
+        sqy[j] = it.qy[q];
+        perm[j] = static_cast<uint32_t>(q);
     }
 }
 
@@ -204,41 +285,51 @@ PassPlan batch_pass(int64_t m, int64_t n_pad, int qpb, int64_t target)
     return pp;
 }
 
-int batch_grid(int sm_count)
+int batch_grid(int sm_count, size_t dyn)
 {
-    static int per_sm = 0;
-    if (!per_sm) {
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32_batch_kernel, kThreads, 0);
-        per_sm = n > 0 ? n : 1;
-    }
-    return per_sm * sm_count;
+    cudaFuncSetAttribute(f32_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(dyn));
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32_batch_kernel, kThreads, dyn);
+    return (n > 0 ? n : 1) * sm_count;
 }
 
 }  // namespace
 
+// Phase-1 plan of a batch item: one pruned unit per query block when the dataset's tile order
+// fits in shared memory, else split scans.
+PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, bool *cull)
+{
+    *cull = n_pad / kTileF32Knn <= kMaxCullTiles;
+    const int qk = kThreads * (kp <= 16 ? 4 : 2);
+    return batch_pass(m, n_pad, qk, *cull ? n_pad : kBatchKnnSplit);
+}
+
 size_t batch_item_bytes(int64_t n_pad, int64_t m, int k)
 {
-    const int kp = kp_for(k);
-    const PassPlan pk = batch_pass(m, n_pad, kThreads * (kp <= 16 ? 4 : 2), kBatchKnnSplit);
+    bool cull;
+    const PassPlan pk = batch_knn_plan(m, n_pad, kp_for(k), &cull);
     const PassPlan pw = batch_pass(m, n_pad, kThreads * kQW32, kBatchWSplit);
     const size_t mm = static_cast<size_t>(m);
     return align256(pk.splits * static_cast<size_t>(k) * mm * sizeof(float)) +
            align256(mm * sizeof(QParamF32)) + align256(pw.splits * 4 * mm * sizeof(float)) +
            sizeof(uint32_t) * (pk.qblocks + 1 + pw.qblocks) + sizeof(BatchItemDev) +
-           sizeof(WorkUnit) * (pk.qblocks * (pk.splits + 1) + pw.qblocks * (pw.splits + 1));
+           sizeof(WorkUnit) * (pk.qblocks * (pk.splits + 1) + pw.qblocks * (pw.splits + 1)) +
+           mm * (6 * sizeof(uint32_t)) + radix_scratch_bytes(m);
 }
 
 // Validates the items and builds the device tables of a batch in library memory.
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
                 BatchState *bs)
 {
-    if (count < 0 || (count > 0 && !items))
+    if (count < 0 || count > 65535 || (count > 0 && !items))
         return AIDW_ERR_INVALID_ARG;
     const int device = ctx_device(ctx);
     std::vector<BatchItemDev> h(count);
     std::vector<size_t> scratch_off(count), cnt_off(count);
     size_t scratch_total = 0, cnt_total = sizeof(uint32_t);  // slot 0: the work counter
+    int64_t total_q = 0, max_m = 0;
+    int max_p2 = 0;
     for (int32_t i = 0; i < count; ++i) {
         const aidw_batch_item &b = items[i];
         DatasetDev dev;
@@ -266,9 +357,19 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.kp = kp_for(b.params.k);
         d.r_exp = r_exp;
         d.am = alpha_map(b.params);
-        const int qk = kThreads * (d.kp <= 16 ? 4 : 2);
-        d.knn = batch_pass(b.m, dev.n_pad, qk, kBatchKnnSplit);
+        bool cull;
+        d.knn = batch_knn_plan(b.m, dev.n_pad, d.kp, &cull);
         d.w = batch_pass(b.m, dev.n_pad, kThreads * kQW32, kBatchWSplit);
+        d.ntiles = static_cast<int32_t>(dev.n_pad / kTileF32Knn);
+        int p2 = 1;
+        while (p2 < d.ntiles)
+            p2 <<= 1;
+        d.ntiles_p2 = cull ? p2 : 0;
+        if (cull && b.m > 0)
+            max_p2 = std::max(max_p2, p2);
+        d.qoff = total_q;
+        total_q += b.m;
+        max_m = std::max<int64_t>(max_m, b.m);
         const size_t m = static_cast<size_t>(b.m);
         scratch_off[i] = scratch_total;
         scratch_total += align256(d.knn.splits * static_cast<size_t>(d.k) * m * sizeof(float)) +
@@ -300,10 +401,13 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         for (int qb = 0; qb < h[i].w.qblocks; ++qb)
             u.push_back({i, qb, 0, kUnitFinal});
 
+    const size_t tq = static_cast<size_t>(std::max<int64_t>(total_q, 1));
     const size_t b_items = align256(sizeof(BatchItemDev) * std::max<int32_t>(count, 1));
     const size_t b_units = align256(sizeof(WorkUnit) * std::max<size_t>(u.size(), 1));
     const size_t b_cnt = align256(cnt_total);
-    bs->bytes = b_items + b_units + b_cnt + scratch_total;
+    const size_t b_q = align256(tq * sizeof(uint32_t));
+    const size_t b_order = 6 * b_q + align256(radix_scratch_bytes(static_cast<int64_t>(tq)));
+    bs->bytes = b_items + b_units + b_cnt + b_order + scratch_total;
     int rc = ctx_alloc(ctx, bs->bytes, st, &bs->block);
     if (rc)
         return rc;
@@ -312,7 +416,15 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     bs->d_units = base + b_items;
     bs->d_counters = reinterpret_cast<uint32_t *>(base + b_items + b_units);
     bs->counter_bytes = cnt_total;
-    char *scratch = base + b_items + b_units + b_cnt;
+    char *ord = base + b_items + b_units + b_cnt;
+    bs->keys = reinterpret_cast<uint32_t *>(ord);
+    bs->vals = reinterpret_cast<uint32_t *>(ord + b_q);
+    bs->item_of = reinterpret_cast<uint32_t *>(ord + 2 * b_q);
+    bs->perm = reinterpret_cast<uint32_t *>(ord + 3 * b_q);
+    bs->sqx = reinterpret_cast<float *>(ord + 4 * b_q);
+    bs->sqy = reinterpret_cast<float *>(ord + 5 * b_q);
+    bs->sort_tmp = ord + 6 * b_q;
+    char *scratch = ord + b_order;
     for (int32_t i = 0; i < count; ++i) {
         BatchItemDev &d = h[i];
         const size_t m = static_cast<size_t>(d.m);
@@ -322,14 +434,21 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.qparam = reinterpret_cast<QParamF32 *>(p);
         p += align256(m * sizeof(QParamF32));
         d.part_sum = reinterpret_cast<float *>(p);
+        d.sqx = bs->sqx + d.qoff;
+        d.sqy = bs->sqy + d.qoff;
+        d.perm = bs->perm + d.qoff;
         uint32_t *c = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(bs->d_counters) +
                                                    cnt_off[i]);
         d.cnt_knn = c;
         d.cnt_sel = c + d.knn.qblocks;
         d.cnt_w = c + d.knn.qblocks + 1;
     }
+    bs->count = count;
+    bs->total_q = total_q;
+    bs->max_m = max_m;
+    bs->dyn_smem = sizeof(unsigned long long) * static_cast<size_t>(std::max(max_p2, 1));
     bs->n_units = static_cast<int>(u.size());
-    bs->grid = batch_grid(ctx_sm_count(ctx));
+    bs->grid = batch_grid(ctx_sm_count(ctx), bs->dyn_smem);
     bool ok = true;
     if (count > 0)
         ok &= cudaMemcpyAsync(bs->d_items, h.data(), sizeof(BatchItemDev) * count,
@@ -337,8 +456,8 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     if (!u.empty())
         ok &= cudaMemcpyAsync(bs->d_units, u.data(), sizeof(WorkUnit) * u.size(),
                               cudaMemcpyHostToDevice, st) == cudaSuccess;
-    // Pageable sources: the copies have completed when cudaMemcpyAsync returns for the host
-    // side, but the device side is ordered on `st` before the kernel.
+    // The copies read pageable host memory: they are staged before cudaMemcpyAsync returns,
+    // and ordered on `st` before the kernels.
     if (!ok) {
         ctx_free(ctx, bs->block, bs->bytes, st);
         bs->block = nullptr;
@@ -347,16 +466,31 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     return AIDW_OK;
 }
 
-// Stream-ordered: zero the counters, run the persistent kernel.
+// Stream-ordered: order the queries, zero the counters, run the persistent kernel.
 int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st)
 {
     if (bs.n_units == 0)
         return AIDW_OK;
+    const BatchItemDev *items = static_cast<const BatchItemDev *>(bs.d_items);
+    const int64_t tq = bs.total_q;
+    const unsigned gx = static_cast<unsigned>(std::min<int64_t>((bs.max_m + 255) / 256, 64));
+    batch_keys_kernel<<<dim3(std::max(gx, 1u), bs.count), 256, 0, st>>>(items, bs.keys, bs.vals,
+                                                                         bs.item_of);
+    if (cudaGetLastError() != cudaSuccess ||
+        radix_sort_pairs(bs.keys, bs.vals, tq, bs.sort_tmp, st, 32) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    const unsigned g1 = static_cast<unsigned>(std::min<int64_t>((tq + 255) / 256, 4096));
+    batch_item_keys_kernel<<<std::max(g1, 1u), 256, 0, st>>>(bs.vals, bs.item_of, tq, bs.keys);
+    if (cudaGetLastError() != cudaSuccess ||
+        radix_sort_pairs(bs.keys, bs.vals, tq, bs.sort_tmp, st, 16) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    batch_gather_kernel<<<std::max(g1, 1u), 256, 0, st>>>(items, bs.vals, bs.item_of, tq,
+                                                          bs.sqx, bs.sqy, bs.perm);
     if (cudaMemsetAsync(bs.d_counters, 0, bs.counter_bytes, st) != cudaSuccess)
         return AIDW_ERR_CUDA;
-    f32_batch_kernel<<<bs.grid, kThreads, 0, st>>>(
-        static_cast<const BatchItemDev *>(bs.d_items), static_cast<const WorkUnit *>(bs.d_units),
-        bs.n_units, bs.d_counters, ctx_err_word(ctx));
+    f32_batch_kernel<<<bs.grid, kThreads, bs.dyn_smem, st>>>(
+        items, static_cast<const WorkUnit *>(bs.d_units), bs.n_units, bs.d_counters,
+        ctx_err_word(ctx));
     return cudaGetLastError() == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
 }
 

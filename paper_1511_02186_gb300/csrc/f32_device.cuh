@@ -255,6 +255,220 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
 }
 
 // ---------------------------------------------------------------------------------------------
+// Phase 1 over Z-ordered queries, one CTA per query block and no data splits. The CTA takes the
+// bounding box of its queries, computes for every data tile a lower bound of the squared
+// distance between the two boxes, sorts the tiles by it (bitonic sort in shared memory) and
+// visits them nearest first. After each tile it takes T = the largest k-th squared distance of
+// its queries; it stops at the first tile whose bound exceeds T. No skipped point could enter a
+// list: its exact FP32 distance is at least the box bound (the bound is shrunk by 2^-20 to
+// cover rounding), which exceeds every query's current k-th distance.
+// ---------------------------------------------------------------------------------------------
+constexpr float kBoundShrink = 1.0f - 9.5367431640625e-07f;  // 1 - 2^-20
+
+// Shared-memory scratch of a pruned phase-1 unit.
+struct CullShared {
+    float red[4][kThreads / 32];
+    float4 box;
+    float thr;
+    int issued;
+};
+
+// Phase-1 unit over one block of Z-ordered queries (qbase..), all data tiles, pruned as above.
+// `order` holds ntiles_p2 (a power of two >= ntiles) 64-bit keys in shared memory. Returns false
+// if a tile wait timed out (the error word is then set).
+template <int KP, int Q, bool IDX>
+__device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, int64_t qbase,
+                                              int ntiles, int ntiles_p2,
+                                              const float *__restrict__ sqx,
+                                              const float *__restrict__ sqy, int k,
+                                              float *__restrict__ part_d2,
+                                              int32_t *__restrict__ part_idx,
+                                              int *__restrict__ err,
+                                              float4 (*tile)[kTileF32Knn], TileSeq &ts,
+                                              unsigned long long *order, int32_t *idx_smem,
+                                              CullShared &cs)
+{
+    constexpr int H = Q / 2;
+    constexpr int W = kThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float (*red)[W] = cs.red;
+
+    float2 qxp[H], qyp[H], nthr[H];
+    float L[Q][KP];
+    float bx0 = CUDART_INF_F, by0 = CUDART_INF_F, bx1 = -CUDART_INF_F, by1 = -CUDART_INF_F;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        const float a = sqx[q], b = sqy[q];
+        bx0 = fminf(bx0, a);
+        by0 = fminf(by0, b);
+        bx1 = fmaxf(bx1, a);
+        by1 = fmaxf(by1, b);
+        if (j & 1) {
+            qxp[j / 2].y = a;
+            qyp[j / 2].y = b;
+        } else {
+            qxp[j / 2].x = a;
+            qyp[j / 2].x = b;
+        }
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+            L[j][i] = (i < KP - k) ? -CUDART_INF_F : CUDART_INF_F;
+        if (IDX) {
+#pragma unroll
+            for (int i = 0; i < KP; ++i)
+                idx_smem[(j * KP + i) * kThreads + tid] = -1;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        nthr[h] = make_float2(-CUDART_INF_F, -CUDART_INF_F);
+    for (int o = 16; o > 0; o >>= 1) {
+        bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+        by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+        bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+        by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+    }
+    if (lane == 0) {
+        red[0][warp] = bx0;
+        red[1][warp] = by0;
+        red[2][warp] = bx1;
+        red[3][warp] = by1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float4 b = make_float4(red[0][0], red[1][0], red[2][0], red[3][0]);
+        for (int w = 1; w < W; ++w) {
+            b.x = fminf(b.x, red[0][w]);
+            b.y = fminf(b.y, red[1][w]);
+            b.z = fmaxf(b.z, red[2][w]);
+            b.w = fmaxf(b.w, red[3][w]);
+        }
+        cs.box = b;
+        cs.thr = CUDART_INF_F;
+    }
+    __syncthreads();
+    const float4 qb = cs.box;
+    // Lower bounds of the box-to-box squared distance, keyed for an ascending sort.
+    for (int t = tid; t < ntiles_p2; t += kThreads) {
+        unsigned long long key = ~0ull;
+        if (t < ntiles) {
+            const float4 tb = ds.tile_box[t];
+            const float dx = fmaxf(0.0f, fmaxf(tb.x - qb.z, qb.x - tb.z));
+            const float dy = fmaxf(0.0f, fmaxf(tb.y - qb.w, qb.y - tb.w));
+            const float lb = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), kBoundShrink);
+            key = (static_cast<unsigned long long>(__float_as_uint(lb)) << 32) |
+                  static_cast<unsigned long long>(t);
+        }
+        order[t] = key;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= ntiles_p2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < ntiles_p2; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = order[i], b = order[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((a > b) == up) {
+                        order[i] = b;
+                        order[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    constexpr uint32_t kBytes = kTileF32Knn * sizeof(float4);
+    if (tid == 0) {
+        int issued = 0;
+        for (; issued < 2 && issued < ntiles; ++issued) {
+            const int64_t t = static_cast<int64_t>(order[issued] & 0xffffffffull);
+            const uint32_t b = (ts.seq + issued) & 1;
+            mbar_arrive_expect_tx(&ts.bar[b], kBytes);
+            tma_load_1d(tile[b], ds.nxy2 + t * kTileF32Knn, kBytes, &ts.bar[b]);
+        }
+        cs.issued = issued;
+    }
+    __syncthreads();
+    int i = 0;
+    bool ok = true;
+    for (; i < ntiles; ++i) {
+        const unsigned long long key = order[i];
+        if (__uint_as_float(static_cast<uint32_t>(key >> 32)) > cs.thr)
+            break;
+        const uint32_t sq = ts.seq + i;
+        const int b = sq & 1;
+        const bool got = mbar_wait(&ts.bar[b], (sq >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            break;
+        }
+        const int64_t t = static_cast<int64_t>(key & 0xffffffffull);
+        knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem);
+        float mx = -CUDART_INF_F;
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            mx = fmaxf(mx, L[j][KP - 1]);
+        for (int o = 16; o > 0; o >>= 1)
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0)
+            red[0][warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            float v = red[0][0];
+            for (int w = 1; w < W; ++w)
+                v = fmaxf(v, red[0][w]);
+            cs.thr = v;
+            const int nx = i + 2;
+            if (nx < ntiles &&
+                __uint_as_float(static_cast<uint32_t>(order[nx] >> 32)) <= v) {
+                const int64_t tn = static_cast<int64_t>(order[nx] & 0xffffffffull);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&ts.bar[b], kBytes);
+                tma_load_1d(tile[b], ds.nxy2 + tn * kTileF32Knn, kBytes, &ts.bar[b]);
+                cs.issued = nx + 1;
+            }
+        }
+        __syncthreads();
+    }
+    // Wait (bounded) for tiles issued but not consumed before leaving.
+    const int issued = cs.issued;
+    if (tid == 0) {
+        for (int u = i; u < issued; ++u) {
+            const uint32_t sq = ts.seq + u;
+            (void)mbar_wait(&ts.bar[sq & 1], (sq >> 1) & 1);
+        }
+        if (!ok)
+            atomicOr(err, kErrTimeout);
+    }
+    ts.seq += issued;
+    __syncthreads();
+    if (!ok)
+        return false;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = qbase + j * kThreads + tid;
+        if (q >= m)
+            continue;
+#pragma unroll
+        for (int r0 = 0; r0 < KP; ++r0) {
+            const int r = r0 - (KP - k);
+            if (r >= 0) {
+                const int64_t o = static_cast<int64_t>(r) * m + q;
+                part_d2[o] = L[j][r0];
+                if (IDX) {
+                    const int32_t v = idx_smem[(j * KP + r0) * kThreads + tid];
+                    part_idx[o] = v >= 0 ? ds.orig[v] : -1;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Selection of one query: merge the S split lists (ties to the lower index), r_obs (Eq. 3) as an
 // FP32 pairwise sum of the k distances, R (Eq. 4 with r_exp of Eq. 2), mu (Eq. 5) and alpha
 // (Eq. 6) in FP64, then the phase-2 parameters. Split lists are read with L2-coherent loads so

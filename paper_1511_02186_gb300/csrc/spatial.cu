@@ -19,27 +19,6 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per block and pass
 
-// Spreads the low 16 bits of v to the even bit positions.
-__device__ __forceinline__ uint32_t spread16(uint32_t v)
-{
-    v &= 0xffffu;
-    v = (v | (v << 8)) & 0x00ff00ffu;
-    v = (v | (v << 4)) & 0x0f0f0f0fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
-
-__device__ __forceinline__ uint32_t morton_of(float x, float y, float4 box)
-{
-    // 16-bit cells over the box; values outside (or NaN) clamp to the edges.
-    const float sx = box.z > box.x ? 65535.0f / (box.z - box.x) : 0.0f;
-    const float sy = box.w > box.y ? 65535.0f / (box.w - box.y) : 0.0f;
-    const float fx = fminf(fmaxf((x - box.x) * sx, 0.0f), 65535.0f);
-    const float fy = fminf(fmaxf((y - box.y) * sy, 0.0f), 65535.0f);
-    return (spread16(static_cast<uint32_t>(fy)) << 1) | spread16(static_cast<uint32_t>(fx));
-}
-
 // Order-preserving map of floats to unsigned integers (for atomic min / max).
 __device__ __forceinline__ uint32_t f2ord(float f)
 {
@@ -250,9 +229,11 @@ size_t radix_scratch_bytes(int64_t n)
     return sizeof(uint32_t) * (2 * static_cast<size_t>(n) + 256 * static_cast<size_t>(nblocks));
 }
 
-// Sorts (keys, vals)[0..n) by key, stably; tmp holds radix_scratch_bytes(n) bytes.
+// Sorts (keys, vals)[0..n) stably by the low `bits` bits of the key (rounded up to a multiple
+// of 16, so that an even number of 8-bit passes leaves the result in place); tmp holds
+// radix_scratch_bytes(n) bytes.
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tmp,
-                             cudaStream_t st)
+                             cudaStream_t st, int bits)
 {
     if (n <= 1)
         return cudaSuccess;
@@ -261,7 +242,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tm
     uint32_t *v2 = k2 + n;
     uint32_t *counts = v2 + n;
     uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
-    for (int shift = 0; shift < 32; shift += 8) {
+    const int top = bits <= 16 ? 16 : 32;
+    for (int shift = 0; shift < top; shift += 8) {
         radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, n, shift, counts, nblocks);
         radix_scan_kernel<<<1, 1024, 0, st>>>(counts, static_cast<int64_t>(nblocks) * 256);
         radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts,
@@ -273,7 +255,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tm
         va = vb;
         vb = t;
     }
-    return cudaGetLastError();  // four passes: the result is back in keys / vals
+    return cudaGetLastError();  // an even number of passes: the result is back in keys / vals
 }
 
 // Bounding box of n points of an interleaved array into *box (device), using 16 bytes of
