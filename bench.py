@@ -41,6 +41,25 @@ FP32_OPS_P2, MUFU_OPS_P2 = 7, 2
 LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
+    kernel's sources changed since the capture (the counters would no longer describe it)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "weights_kernel_traffic_uniform_1Mx1M.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if not rec["kernel"].startswith(kernel):
+            return None
+        for rel, sha in rec["source_sha1"].items():
+            with open(os.path.join(ROOT, rel), "rb") as g:
+                if hashlib.sha1(g.read()).hexdigest() != sha:
+                    return None
+        return rec["dram_read_bytes"] + rec["dram_write_bytes"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload_config(wl):
     name = "uniform_paper_1M_x_1M" if wl.n == N_DATA and wl.m == M_QUERY else \
         f"uniform_paper_{wl.n}_x_{wl.m}"
@@ -448,7 +467,10 @@ def run_gpu(args):
                      "query_blocks": ktimes[0].query_blocks},
             "roofline": {"bound": "alu", "kernel": f"f32_{dominant}_kernel",
                          "achieved": achieved, "peak": peak, "unit": UNIT,
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (measured_traffic("f32_weights_kernel")
+                                     if wl.n == N_DATA and wl.m == M_QUERY else None),
+                         "traffic_unit": "bytes per launch (ncu, committed capture)",
                          "peak_basis": (f"{sm} SMs x {sm_mhz_peak:.0f} MHz (max SM clock) / "
                                         "max(7 FP32 ops / 128 lanes, 1/ex2 + 1/lg2 measured MUFU "
                                         "rates per clk per SM, 9 instructions / 128 issue slots)"

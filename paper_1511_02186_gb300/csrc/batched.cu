@@ -109,8 +109,10 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
 {
     extern __shared__ unsigned long long order[];  // tile order of a KNN unit
     __shared__ CullShared cs;
-    __shared__ __align__(128) float4 ktile[2][kTileF32Knn];
+    // Phase-1 and phase-2 units take turns on the same coordinate tile buffers.
+    static_assert(kTileF32Knn == kTileF32W, "shared tile buffers");
     __shared__ __align__(128) float4 txy[2][kTileF32W];
+    float4(*ktile)[kTileF32Knn] = txy;
     __shared__ __align__(128) float2 tz[2][kTileF32W];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_unit, s_flag;
