@@ -224,7 +224,8 @@ def oracle_rate_small(wl, threads):
 def bench_batched(ctx, steps: int, warmup: int, dev, stream):
     """256 independent datasets (n log-uniform in [1,024, 262,144], m log-uniform in
     [1,024, 65,536], side log-uniform in [10, 1000], uniform or clustered, k in {6, 10, 15}) in
-    one persistent launch replayed from a CUDA graph."""
+    one persistent launch replayed from a CUDA graph: timed with the built-in kernel shape,
+    then autotuned on the batch itself and timed again with the winning shape."""
     import torch
     from paper_1511_02186_gb300 import aidw, workloads
     wls = workloads.batched(0)
@@ -237,45 +238,59 @@ def bench_batched(ctx, steps: int, warmup: int, dev, stream):
         items.append((ds, qx, qy, aidw.default_params(k=wl.k), out, None))
     pairs = float(sum(wl.n * wl.m for wl in wls))
     pb = ctx.batch_create(items)
-    for _ in range(max(1, warmup)):
-        pb.launch(stream.cuda_stream)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(steps)]
-    for a, b in evs:
-        a.record(stream)
-        pb.launch(stream.cuda_stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in evs]
+
+    def timed():
+        for _ in range(max(1, warmup)):
+            pb.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            pb.launch(stream.cuda_stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+    ms_default = timed()
+    t0 = time.perf_counter()
+    cfg, tune_ms = pb.autotune(reps=2)
+    tune_s = time.perf_counter() - t0
+    ms = timed()
     pb.destroy()
     for it in items:
         it[0].destroy()
     return {"workload": "batched_256_datasets", "datasets": len(wls),
             "pair_evals_per_launch": pairs, "launches": steps,
-            "ms_per_launch": statistics.mean(ms),
-            "value": pairs / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "ms_per_launch": ms,
+            "value": pairs / (ms / 1e3), "unit": UNIT,
             "queries": int(sum(wl.m for wl in wls)),
-            "launch": "one persistent work-queue kernel per batch, replayed from a CUDA graph"}
+            "tuned_config": cfg.as_dict(), "autotune_s": tune_s,
+            "default_config_ms_per_launch": ms_default,
+            "default_config_value": pairs / (ms_default / 1e3),
+            "launch": "one persistent work-queue kernel per batch, replayed from a CUDA graph; "
+                      "kernel shape chosen by the autotuner on this batch"}
 
 
 def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s: float):
     """64 resident datasets (n log-uniform in [16K, 1M]); Poisson arrivals of requests with
     256..262,144 query points (log-uniform, host arrays) uniform in the dataset's square.
-    Two runs: a sustainable rate (half the measured capacity) and the nominal 2,000 req/s."""
+    Runs at 0.25, 0.5 and 0.8 of the measured single-launch capacity and at the nominal
+    2,000 req/s (an offered load several times the capacity: admission and backpressure),
+    then serves a prefix of the same request stream one request per launch (FP64 and FP32,
+    no batching) for comparison."""
     from paper_1511_02186_gb300 import aidw, workloads
     dsw = workloads.served_datasets(0)
     handles = [ctx.create_dataset(w.x, w.y, w.z, w.area) for w in dsw]
     p = aidw.default_params(k=10)
-    results = {}
-    mean_pairs = None
-    for label, rate, window in (("sustained", None, window_s),
-                                ("nominal_2000_per_s", 2000.0, nominal_window_s)):
-        if rate is None:
-            probe = workloads.served_requests(dsw, seed=11, rate=2000.0, duration_s=1.0)
-            mean_pairs = statistics.mean(dsw[d].n * len(qx) for _, d, qx, _ in probe)
-            rate = max(1.0, 0.5 * capacity_pairs_s / mean_pairs)
-        reqs = workloads.served_requests(dsw, seed=12, rate=rate, duration_s=window)
+    probe = workloads.served_requests(dsw, seed=11, rate=2000.0, duration_s=1.0)
+    mean_pairs = statistics.mean(dsw[d].n * len(qx) for _, d, qx, _ in probe)
+    results = {"mean_pair_evals_per_request": mean_pairs}
+    runs = [(f"load_{f:.2f}_of_capacity", max(1.0, f * capacity_pairs_s / mean_pairs), window_s,
+             12 + i) for i, f in enumerate((0.25, 0.5, 0.8))]
+    runs.append(("nominal_2000_per_s", 2000.0, nominal_window_s, 20))
+    for label, rate, window, seed in runs:
+        reqs = workloads.served_requests(dsw, seed=seed, rate=rate, duration_s=window)
         prepared = [(t, d, qx.astype(np.float32), qy.astype(np.float32),
                      np.empty(len(qx), dtype=np.float32)) for t, d, qx, qy in reqs]
         ids = []
@@ -306,14 +321,102 @@ def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s
                           "max_ms": float(lat.max()),
                           "throughput": pairs / wall, "unit": UNIT,
                           "offered": rate * mean_pairs, "resubmits_after_again": again}
+    results["sustained"] = results["load_0.50_of_capacity"]
     st = ctx.serving_stats()
     results["launches"] = int(st.launches)
     results["max_concurrent_launches"] = int(st.max_concurrent_launches)
     results["mean_requests_per_launch"] = st.batched_requests / max(1, st.launches)
     results["workload"] = "served_64_datasets_poisson"
+
+    # Unbatched launches of the same request stream (a prefix bounded to about 4e10
+    # pair-evaluations, i.e. a few seconds of FP64 work), one synchronous call per request.
+    prefix, acc = [], 0.0
+    for _, d, qx, qy in workloads.served_requests(dsw, seed=13, rate=1000.0, duration_s=2.0):
+        if prefix and acc + dsw[d].n * len(qx) > 4e10:
+            break
+        prefix.append((d, qx, qy))
+        acc += dsw[d].n * len(qx)
+    for label, prec in (("unbatched_fp64", aidw.F64), ("unbatched_fp32", aidw.F32C)):
+        pp = aidw.default_params(k=10, precision=prec)
+        dt = np.float64 if prec == aidw.F64 else np.float32
+        reqs = [(d, qx.astype(dt), qy.astype(dt), np.empty(len(qx), dtype=dt))
+                for d, qx, qy in prefix]
+        svc = []
+        t0 = time.perf_counter()
+        for d, qx, qy, out in reqs:
+            t1 = time.perf_counter()
+            ctx.interpolate(handles[d], qx, qy, pp, out=out)
+            svc.append(time.perf_counter() - t1)
+        wall = time.perf_counter() - t0
+        svc_ms = np.array(svc) * 1e3
+        results[label] = {"requests": len(reqs), "pair_evals": acc,
+                          "throughput": acc / wall, "unit": UNIT,
+                          "p50_service_ms": float(np.percentile(svc_ms, 50)),
+                          "p99_service_ms": float(np.percentile(svc_ms, 99)),
+                          "launch": "one aidw_interpolate per request, host arrays, "
+                                    "back to back"}
     for h in handles:
         h.destroy()
     return results
+
+
+def bench_precision_stress(ctx, dev, stream):
+    """The clustered precision-stress workload: 2,097,152 data points (90 % from 32 Gaussians,
+    sigma 5-50, 10 % uniform) in [0,1000]^2, queries on the 1448 x 1448 cell-centre grid,
+    z lognormal(0, 1), k = 10. One FP32 launch over all queries (timed), its error against the
+    FP64 oracle on 768 queries (256 seeded, plus the 256 smallest and 256 largest alpha), and
+    the FP64 GPU path on 2,048 seeded queries."""
+    import torch
+    import oracle
+    from paper_1511_02186_gb300 import aidw, workloads
+    wl = workloads.clustered_grid(0)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)
+    qy = torch.as_tensor(wl.qy, dtype=torch.float32, device=dev)
+    out = torch.empty(wl.m, dtype=torch.float32, device=dev)
+    oa = torch.empty(wl.m, dtype=torch.float32, device=dev)
+    p = aidw.default_params(k=wl.k, levels=wl.levels)
+    ctx.interpolate(ds, qx, qy, p, out=out, out_alpha=oa, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.interpolate(ds, qx, qy, p, out=out, out_alpha=oa, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    z = out.cpu().numpy().astype(np.float64)
+    alpha = oa.cpu().numpy()
+    order = np.argsort(alpha, kind="stable")
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([rng.choice(wl.m, 256, replace=False), order[:256],
+                                    order[-256:]]))
+    w32 = wl.as_f32()
+    ref = oracle.interpolate(w32.x, w32.y, w32.z, w32.area, w32.qx[idx], w32.qy[idx], w32.k,
+                             w32.levels, w32.r_min, w32.r_max)
+    den = np.maximum(np.abs(ref["z"]), ref["scale"])
+    err = np.abs(z[idx] - ref["z"]) / den
+    pure = np.abs(z[idx] - ref["z"]) / np.abs(ref["z"])
+    q64 = 2048
+    i64 = torch.as_tensor(np.random.default_rng(32).choice(wl.m, q64, replace=False), device=dev)
+    qx64 = torch.as_tensor(wl.qx, dtype=torch.float64, device=dev)[i64].contiguous()
+    qy64 = torch.as_tensor(wl.qy, dtype=torch.float64, device=dev)[i64].contiguous()
+    p64 = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64)
+    ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
+    e0.record(stream)
+    ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    ds.destroy()
+    return {"workload": "clustered_2097152_grid_1448x1448", "n": wl.n, "m": wl.m,
+            "fp32_ms": ms, "value": wl.n * wl.m / (ms / 1e3), "unit": UNIT,
+            "alpha_range": [float(alpha.min()), float(alpha.max())],
+            "max_rel_err_vs_fp64_oracle": float(err.max()),
+            "max_pure_rel_err_vs_fp64_oracle": float(pure.max()),
+            "error_sample": f"{len(idx)} queries (256 seeded, 256 smallest and 256 largest "
+                            "alpha) against the oracle on the FP32-rounded inputs",
+            "tolerance": 1e-5,
+            "fp64_path": {"value": q64 * wl.n / (ms64 / 1e3), "unit": UNIT,
+                          "sample": f"{q64} seeded queries x all {wl.n} data points"}}
 
 
 # ---- GPU arm -----------------------------------------------------------------------------------
@@ -443,6 +546,7 @@ def run_gpu(args):
     d2h = 4 * wl.m
 
     batched = bench_batched(ctx, max(2, args.steps), args.warmup, dev, stream)
+    stress = bench_precision_stress(ctx, dev, stream)
     served = None
     if world == 1 or rank == 0:
         sctx = aidw.Context(local)
@@ -491,14 +595,21 @@ def run_gpu(args):
                     "includes": "dataset upload + conversion, query upload, both phases, "
                                 "result download"},
             "batched": batched,
+            "precision_stress": stress,
             "served": served,
             "gpu_launches": sum(t.launches for t in ktimes),
             "clocks": clk,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads,
                              "kind": "oracle", "sample": cpu_sample},
             "paper_context": {"gt730m_tiled_soa_1000K_pair_evals_s": 6.2e9,
-                              "note": "GeForce GT 730M, FP32, N = 1,024,000, transfers "
-                                      "included; different hardware and workload"},
+                              "speedups_over_serial_cpu": {"fp32_naive": 270, "fp32_tiled": 400,
+                                                           "fp64": 8},
+                              "this_build_over_cpu_oracle": {
+                                  "fp32": value / cpu_v, "fp64": fp64_rate / cpu_v},
+                              "note": "paper: GeForce GT 730M vs one core of an Intel Core "
+                                      "i7-4700MQ, N = 1,024,000, transfers included; here: "
+                                      "GB300 vs the FP64 oracle on all host cores; different "
+                                      "hardware, baselines and workload"},
         }
     ds.destroy()
     ctx.close()

@@ -176,6 +176,81 @@ int aidw_batch_create(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count
 int aidw_batch_launch(aidw_ctx *ctx, aidw_batch *batch, void *stream);
 int aidw_batch_destroy(aidw_ctx *ctx, aidw_batch *batch);
 
+/* ---- kernel shapes and the autotuner ---------------------------------------------------- */
+/* The shape of the FP32 kernels (the paper fixes none: Sec. 3.1.1 tiles data through shared
+ * memory for a block of queries; sizes are the implementation's). Every field except
+ * split_points is arithmetic-neutral: the per-query operations and their order do not depend
+ * on it, so results are bit-identical across its values. split_points (and, in aidw_interpolate,
+ * the phase-2 split count that occupancy picks for a query-block size) regroups the FP32 partial
+ * sums of Eq. 1, which changes results only within the FP32 tolerance. */
+typedef struct aidw_tune_config {
+    int32_t queries_per_thread; /* phase 2: 2, 4 or 8 queries per thread (query block 128x) */
+    int32_t tile_points;        /* phase 2: data points per shared-memory tile, 256 or 512 */
+    int32_t knn_list;           /* phase 1: k-list register length at least this: 0 (the
+                                 * smallest of 8, 12, 16, 32 that holds k), 16 or 32 */
+    int32_t split_points;       /* batches: data points per phase-2 work unit, a multiple of
+                                 * 2,048 in [2,048, 4,194,304] */
+    int32_t ctas_per_sm;        /* batches: persistent CTAs per SM, 0 = as many as fit */
+    int32_t reserved[3];        /* zero */
+} aidw_tune_config;
+
+/* Fills the built-in shape: 4 queries per thread, 512-point tiles, the smallest list, 65,536
+ * points per batch work unit, full occupancy. */
+int aidw_tune_config_default(aidw_tune_config *out);
+/* AIDW_OK if every field is one of the values above, else AIDW_ERR_INVALID_ARG. */
+int aidw_tune_config_check(const aidw_tune_config *cfg);
+
+/* The context's shape, used by aidw_interpolate (FP32), aidw_interpolate_noalloc,
+ * aidw_interpolate_batch and new prepared batches; the serving runtime keeps the shape the
+ * context had when it started. Set it between calls, not while work is queued. */
+int aidw_set_tune_config(aidw_ctx *ctx, const aidw_tune_config *cfg);
+int aidw_get_tune_config(aidw_ctx *ctx, aidw_tune_config *out);
+
+/* Autotuner flags. AIDW_TUNE_CACHE: look the workload's key up in the process-wide tuning cache
+ * first (a hit is used without timing: *best_ms = -1, one untimed run for
+ * aidw_autotune_interpolate, none for batches) and store the winner under it.
+ * AIDW_TUNE_APPLY (aidw_autotune_interpolate): make the winner the context's shape. */
+#define AIDW_TUNE_CACHE 1u
+#define AIDW_TUNE_APPLY 2u
+
+/* Times an FP32 interpolation (arguments as aidw_interpolate, device arrays only) under
+ * candidate shapes by coordinate search from the context's shape (queries per thread, tile
+ * points, k-list length; each candidate run `reps` times after one warm-up, fastest run
+ * counts) and returns the fastest in *best with its time in *best_ms. `out` receives the
+ * results of the last run. Synchronous. Errors: as aidw_interpolate; INVALID_ARG for host
+ * arrays, F64 or reps < 1. */
+int aidw_autotune_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy,
+                              int64_t m, const aidw_params *p, void *out, int32_t reps,
+                              uint32_t flags, aidw_tune_config *best, double *best_ms);
+
+/* Rebuilds a prepared batch under `cfg` (work list, scratch and graph). */
+int aidw_batch_set_config(aidw_ctx *ctx, aidw_batch *batch, const aidw_tune_config *cfg);
+int aidw_batch_get_config(aidw_ctx *ctx, aidw_batch *batch, aidw_tune_config *out);
+
+/* Times the prepared batch under candidate shapes by coordinate search from its current one
+ * (queries per thread, tile points, k-list length, points per work unit, CTAs per SM; each
+ * candidate launched `reps` times after one warm-up, fastest launch counts), leaves the batch
+ * prepared with the fastest and returns it. Synchronous; after a search the batch's outputs
+ * hold the winner's results. Errors: INVALID_ARG, NOT_FOUND (a dataset was destroyed), OOM,
+ * CUDA, TIMEOUT (an on-device wait ran out). */
+int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *batch, int32_t reps, uint32_t flags,
+                        aidw_tune_config *best, double *best_ms);
+
+/* Process-wide tuning cache: workload keys (printable ASCII without '"' or '\\', at most 255
+ * characters; the autotuner's keys name the device and the workload's size class) mapped to
+ * shapes. Files hold one JSON object per line:
+ *   {"key": "...", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
+ *    "split_points": 65536, "ctas_per_sm": 0, "ms": 91.5}
+ * _load merges a file into the cache (INVALID_ARG on a malformed line, NOT_FOUND if the file
+ * cannot be opened; nothing is merged on error); _save writes the whole cache; _get returns
+ * NOT_FOUND for an unknown key. Host only: usable without a GPU. */
+int aidw_tune_cache_put(const char *key, const aidw_tune_config *cfg, double ms);
+int aidw_tune_cache_get(const char *key, aidw_tune_config *out, double *ms);
+int aidw_tune_cache_clear(void);
+int aidw_tune_cache_size(void);
+int aidw_tune_cache_save(const char *path);
+int aidw_tune_cache_load(const char *path);
+
 /* ---- serving: asynchronous requests with continuous batching --------------------------- */
 /* Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host
  * or device and must stay valid until aidw_poll/aidw_wait report completion). The context's
@@ -266,6 +341,14 @@ int aidw_measure_pipe_rates(aidw_ctx *ctx, aidw_pipe_rates *out);
 /* Test hook (host-side fault injection): the `after`-th device allocation from now fails with
  * AIDW_ERR_OOM; after < 0 disables it. */
 int aidw_debug_fail_alloc_after(aidw_ctx *ctx, int64_t after);
+
+/* Test hook for the bounded on-device waits: runs one CTA that waits, with the scans' own wait
+ * code and a limit of `polls` polls (1 .. 2^20), on something that never completes (which = 0:
+ * an mbarrier tile wait with no arrival; which = 1: another CTA's counter that is never
+ * incremented). The wait runs out, the kernel raises the context's error word and returns, so
+ * the next aidw_check_device_errors (or synchronous call) returns AIDW_ERR_TIMEOUT and the
+ * context stays usable. Synchronous; returns AIDW_OK once the kernel has finished. */
+int aidw_debug_expire_wait(aidw_ctx *ctx, int32_t which, uint32_t polls);
 
 #ifdef __cplusplus
 }

@@ -80,6 +80,29 @@ class BatchItem(ctypes.Structure):
                 ("out_alpha", ctypes.c_void_p)]
 
 
+class TuneConfig(ctypes.Structure):
+    """``aidw_tune_config``: kernel shape (phase-2 queries per thread and tile points, k-list
+    length, points per batched phase-2 unit, persistent CTAs per SM)."""
+    _fields_ = [("queries_per_thread", ctypes.c_int32), ("tile_points", ctypes.c_int32),
+                ("knn_list", ctypes.c_int32), ("split_points", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    FIELDS = ("queries_per_thread", "tile_points", "knn_list", "split_points", "ctas_per_sm")
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f in self.FIELDS}
+
+    def __eq__(self, other):
+        return isinstance(other, TuneConfig) and self.as_dict() == other.as_dict()
+
+    def __repr__(self):
+        return f"TuneConfig({self.as_dict()})"
+
+
+TUNE_CACHE = 1
+TUNE_APPLY = 2
+
+
 # Every symbol of include/aidw.h with its signature (restype, argtypes).
 _P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
@@ -109,6 +132,22 @@ SIGNATURES = {
     "aidw_last_kernel_times": (ctypes.c_int, [_P, _P]),
     "aidw_measure_pipe_rates": (ctypes.c_int, [_P, _P]),
     "aidw_debug_fail_alloc_after": (ctypes.c_int, [_P, _I64]),
+    "aidw_debug_expire_wait": (ctypes.c_int, [_P, _I32, ctypes.c_uint32]),
+    "aidw_tune_config_default": (ctypes.c_int, [_P]),
+    "aidw_tune_config_check": (ctypes.c_int, [_P]),
+    "aidw_set_tune_config": (ctypes.c_int, [_P, _P]),
+    "aidw_get_tune_config": (ctypes.c_int, [_P, _P]),
+    "aidw_autotune_interpolate": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _I32,
+                                                 ctypes.c_uint32, _P, _P]),
+    "aidw_batch_set_config": (ctypes.c_int, [_P, _P, _P]),
+    "aidw_batch_get_config": (ctypes.c_int, [_P, _P, _P]),
+    "aidw_batch_autotune": (ctypes.c_int, [_P, _P, _I32, ctypes.c_uint32, _P, _P]),
+    "aidw_tune_cache_put": (ctypes.c_int, [ctypes.c_char_p, _P, _D]),
+    "aidw_tune_cache_get": (ctypes.c_int, [ctypes.c_char_p, _P, _P]),
+    "aidw_tune_cache_clear": (ctypes.c_int, []),
+    "aidw_tune_cache_size": (ctypes.c_int, []),
+    "aidw_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "aidw_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
 }
 # Test-only hooks exported by the library but not declared in the public header.
 DEBUG_SIGNATURES = {
@@ -155,6 +194,57 @@ def default_params(k: int = 10, levels=(1.0, 2.0, 3.0, 4.0, 5.0), r_min: float =
     p.r_min = float(r_min)
     p.r_max = float(r_max)
     return p
+
+
+def tune_config(**fields) -> TuneConfig:
+    """The built-in kernel shape with the given fields replaced."""
+    c = TuneConfig()
+    _check(load().aidw_tune_config_default(ctypes.byref(c)), "tune_config_default")
+    for k, v in fields.items():
+        if k not in TuneConfig.FIELDS:
+            raise KeyError(k)
+        setattr(c, k, int(v))
+    return c
+
+
+def tune_config_valid(c: TuneConfig) -> bool:
+    return load().aidw_tune_config_check(ctypes.byref(c)) == OK
+
+
+class TuneCache:
+    """The library's process-wide tuning cache (host only)."""
+
+    @staticmethod
+    def put(key: str, cfg: TuneConfig, ms: float = -1.0):
+        _check(load().aidw_tune_cache_put(key.encode(), ctypes.byref(cfg), float(ms)),
+               "tune_cache_put")
+
+    @staticmethod
+    def get(key: str):
+        """(TuneConfig, ms) or None for an unknown key."""
+        c, ms = TuneConfig(), ctypes.c_double()
+        rc = load().aidw_tune_cache_get(key.encode(), ctypes.byref(c), ctypes.byref(ms))
+        if rc == ERR_NOT_FOUND:
+            return None
+        _check(rc, "tune_cache_get")
+        return c, ms.value
+
+    @staticmethod
+    def clear():
+        _check(load().aidw_tune_cache_clear(), "tune_cache_clear")
+
+    @staticmethod
+    def size() -> int:
+        return int(load().aidw_tune_cache_size())
+
+    @staticmethod
+    def save(path: str):
+        _check(load().aidw_tune_cache_save(os.fsencode(path)), "tune_cache_save")
+
+    @staticmethod
+    def load(path: str) -> int:
+        """Merges a cache file; returns the status (OK, ERR_NOT_FOUND, ERR_INVALID_ARG)."""
+        return int(load().aidw_tune_cache_load(os.fsencode(path)))
 
 
 # ---- array marshalling -------------------------------------------------------------------
@@ -222,6 +312,24 @@ class PreparedBatch:
     def launch(self, stream=None):
         st = _stream_of(self.items[0][1], stream) if self.items else 0
         _check(self.ctx.lib.aidw_batch_launch(self.ctx.ptr, self.handle, st), "batch_launch")
+
+    def set_config(self, cfg: TuneConfig):
+        _check(self.ctx.lib.aidw_batch_set_config(self.ctx.ptr, self.handle, ctypes.byref(cfg)),
+               "batch_set_config")
+
+    def config(self) -> TuneConfig:
+        c = TuneConfig()
+        _check(self.ctx.lib.aidw_batch_get_config(self.ctx.ptr, self.handle, ctypes.byref(c)),
+               "batch_get_config")
+        return c
+
+    def autotune(self, reps: int = 2, flags: int = 0):
+        """Times candidate shapes on this batch and keeps the fastest; returns (cfg, ms)."""
+        c, ms = TuneConfig(), ctypes.c_double()
+        _check(self.ctx.lib.aidw_batch_autotune(self.ctx.ptr, self.handle, int(reps),
+                                                int(flags), ctypes.byref(c), ctypes.byref(ms)),
+               "batch_autotune")
+        return c, ms.value
 
     def destroy(self):
         if self.handle:
@@ -343,6 +451,33 @@ class Context:
                "aidw_batch_create")
         return PreparedBatch(self, h, items)
 
+    # -- kernel shapes --
+    def set_tune_config(self, cfg: TuneConfig):
+        _check(self.lib.aidw_set_tune_config(self.ptr, ctypes.byref(cfg)), "set_tune_config")
+
+    def tune_config(self) -> TuneConfig:
+        c = TuneConfig()
+        _check(self.lib.aidw_get_tune_config(self.ptr, ctypes.byref(c)), "get_tune_config")
+        return c
+
+    def autotune_interpolate(self, ds: Dataset, qx, qy, params: Params | None = None, out=None,
+                             reps: int = 2, flags: int = 0):
+        """Times candidate shapes on this FP32 interpolation (CUDA tensors); returns
+        (cfg, ms, out)."""
+        p = params or default_params()
+        kqx, pqx = _prep(qx, "f4")
+        kqy, pqy = _prep(qy, "f4")
+        m = int(kqx.shape[0])
+        if out is None:
+            out = _out_like(qx, (m,), "f4")
+        po = _prep_out(out, "f4")
+        c, ms = TuneConfig(), ctypes.c_double()
+        _check(self.lib.aidw_autotune_interpolate(self.ptr, ds.handle, pqx, pqy, m,
+                                                  ctypes.byref(p), po, int(reps), int(flags),
+                                                  ctypes.byref(c), ctypes.byref(ms)),
+               "autotune_interpolate")
+        return c, ms.value, out
+
     # -- serving --
     def submit(self, ds: Dataset, qx, qy, params: Params, out, out_alpha=None, out_knn=None):
         """Queue a request; returns (status, request id). The query arrays are kept alive by
@@ -407,6 +542,11 @@ class Context:
 
     def check_device_errors(self) -> int:
         return self.lib.aidw_check_device_errors(self.ptr)
+
+    def expire_wait(self, which: int, polls: int = 4096):
+        """Runs a kernel whose bounded wait runs out (0: mbarrier, 1: counter)."""
+        _check(self.lib.aidw_debug_expire_wait(self.ptr, int(which), int(polls)),
+               "expire_wait")
 
     def fail_alloc_after(self, n: int):
         _check(self.lib.aidw_debug_fail_alloc_after(self.ptr, int(n)), "fail_alloc_after")

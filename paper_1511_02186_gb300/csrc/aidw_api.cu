@@ -113,7 +113,8 @@ struct aidw_ctx {
     aidw_kernel_times last{};
     bool last_valid = false;
     int slots_cache[2][4][2] = {};  // [precision][kp bucket][with_idx] knn slots
-    int wslots_cache[2] = {};
+    int wslots_cache[2][3][2] = {};  // [precision][queries per thread 2/4/8][tile 256/512]
+    aidw_tune_config tune = aidw::tune_default();
     ServingRuntime *serving = nullptr;
 };
 
@@ -242,27 +243,31 @@ static PassPlan plan_pass(int64_t m, int64_t n_pad, int qpb, int slots_total, in
     return pp;
 }
 
-static int kp_bucket(int k)
+static int kp_bucket(int kp)
 {
-    return k <= 8 ? 0 : (k <= 12 ? 1 : (k <= 16 ? 2 : 3));
+    return kp <= 8 ? 0 : (kp <= 12 ? 1 : (kp <= 16 ? 2 : 3));
 }
 
 Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bool with_idx,
-               int force_knn_splits, int force_w_splits)
+               int force_knn_splits, int force_w_splits, const aidw_tune_config *cfg)
 {
-    int &ks = ctx->slots_cache[precision][kp_bucket(k)][with_idx ? 1 : 0];
-    if (!ks)
-        ks = precision == AIDW_F64 ? f64_knn_slots_per_sm(k, with_idx)
-                                   : f32_knn_slots_per_sm(k, with_idx);
-    int &ws = ctx->wslots_cache[precision];
-    if (!ws)
-        ws = precision == AIDW_F64 ? f64_w_slots_per_sm() : f32_w_slots_per_sm();
+    const aidw_tune_config &tc = cfg ? *cfg : ctx->tune;
+    const bool f64 = precision == AIDW_F64;
     Plan pl{};
     pl.m = m;
     pl.with_idx = with_idx;
-    const int qk = precision == AIDW_F64 ? f64_knn_queries_per_block(k)
-                                         : f32_knn_queries_per_block(k);
-    const int qw = precision == AIDW_F64 ? f64_w_queries_per_block() : f32_w_queries_per_block();
+    pl.kp = f32_list_length(k, tc.knn_list);
+    pl.qw = tc.queries_per_thread;
+    pl.tw = tc.tile_points;
+    int &ks = ctx->slots_cache[precision][kp_bucket(f64 ? k : pl.kp)][with_idx ? 1 : 0];
+    if (!ks)
+        ks = f64 ? f64_knn_slots_per_sm(k, with_idx) : f32_knn_slots_per_sm(pl.kp, with_idx);
+    int &ws = ctx->wslots_cache[precision][pl.qw == 2 ? 0 : (pl.qw == 4 ? 1 : 2)]
+                               [pl.tw == 256 ? 0 : 1];
+    if (!ws)
+        ws = f64 ? f64_w_slots_per_sm() : f32_w_slots_per_sm(pl.qw, pl.tw);
+    const int qk = f64 ? f64_knn_queries_per_block(k) : f32_knn_queries_per_block(pl.kp);
+    const int qw = f64 ? f64_w_queries_per_block() : f32_w_queries_per_block(pl.qw);
     // A split restarts its neighbour lists: about k (1 + ln(n_split / k)) insertions per query,
     // each a rescan of a chunk by a partly idle warp. Measured on GB300 at n = m = 2^20,
     // k = 10, every extra split costs about as much as scanning 100,000 more points.
@@ -281,6 +286,18 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     force(pl.knn, force_knn_splits);
     force(pl.w, force_w_splits);
     return pl;
+}
+
+aidw_tune_config ctx_tune(aidw_ctx *ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return ctx->tune;
+}
+
+void ctx_set_tune(aidw_ctx *ctx, const aidw_tune_config &c)
+{
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->tune = c;
 }
 
 size_t scratch_bytes(int precision, const Plan &pl, int k)
@@ -474,7 +491,7 @@ int consume_device_error(aidw_ctx *ctx, cudaStream_t st)
 int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const void *qy,
                      int64_t m, const aidw_params *p, void *out, float *out_alpha,
                      int32_t *out_knn, cudaStream_t st, int force_knn_splits,
-                     int force_w_splits)
+                     int force_w_splits, const aidw_tune_config *cfg)
 {
     DatasetDev ds;
     double r_exp;
@@ -513,7 +530,7 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
     }
 
     Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
-                        force_knn_splits, force_w_splits);
+                        force_knn_splits, force_w_splits, cfg);
     const bool cull = force_knn_splits == 0 && use_culled_knn(p->precision, ds, m);
     if (cull) {
         pl.knn.splits = 1;

@@ -28,8 +28,11 @@ constexpr double kEpsF64 = 2.2250738585072014e-308;
 constexpr float kCoincScaleF32 = 1.2676506e30f;  // 2^100
 constexpr double kCoincScaleF64 = 8.452712498170644e270;  // 2^900
 
-// Bounded waits: an mbarrier wait gives up after this many polls and raises the error word.
+// Bounded waits: an mbarrier wait gives up after this many polls and raises the error word;
+// a wait on another CTA's counter gives up after kMaxWaitPolls polls of at least 256 ns
+// (tens of seconds at most).
 constexpr uint32_t kMaxPolls = 1u << 26;
+constexpr uint32_t kMaxWaitPolls = 1u << 26;
 constexpr int kErrTimeout = 1;
 
 // Kernel shape shared by every scan kernel.
@@ -73,6 +76,9 @@ struct Plan {
     PassPlan knn;  // phase 1 scan
     PassPlan w;    // phase 2 scan
     bool with_idx; // keep neighbour indices (needed for the kNN output)
+    int kp;        // FP32 phase 1: register k-list length (8, 12, 16 or 32)
+    int qw;        // FP32 phase 2: queries per thread (2, 4 or 8)
+    int tw;        // FP32 phase 2: data points per shared-memory tile (256 or 512)
 };
 
 // Per-query parameters of phase 2 produced by the selection kernel.
@@ -143,11 +149,17 @@ cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
                                 cudaStream_t st);
 
 // Shape of the kernels: queries per CTA of each scan and the CTA slots per SM that occupancy
-// allows (used to cut splits into whole waves).
-int f32_knn_queries_per_block(int k);
-int f32_w_queries_per_block();
-int f32_knn_slots_per_sm(int k, bool with_idx);
-int f32_w_slots_per_sm();
+// allows (used to cut splits into whole waves). FP32 shapes follow the tuning fields of
+// aidw_tune_config (kp: k-list length, qw: phase-2 queries per thread, tw: tile points).
+int f32_knn_queries_per_block(int kp);
+int f32_w_queries_per_block(int qw);
+int f32_knn_slots_per_sm(int kp, bool with_idx);
+int f32_w_slots_per_sm(int qw, int tw);
+// k-list length for k under a minimum (aidw_tune_config.knn_list).
+int f32_list_length(int k, int kp_min);
+// Built-in shape and the check of a caller's shape (autotune.cu).
+aidw_tune_config tune_default();
+bool tune_valid(const aidw_tune_config &c);
 int f64_knn_queries_per_block(int k);
 int f64_w_queries_per_block();
 int f64_knn_slots_per_sm(int k, bool with_idx);
@@ -199,11 +211,12 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 }
 
 // Bounded wait for phase `parity` of `bar`. Returns false (and leaves the caller to raise
-// the error word) if the phase did not complete within kMaxPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// the error word) if the phase did not complete within max_polls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t max_polls = kMaxPolls)
 {
     uint32_t addr = smem_addr(bar);
-    for (uint32_t i = 0; i < kMaxPolls; ++i) {
+    for (uint32_t i = 0; i < max_polls; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -216,6 +229,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
             return true;
     }
     return false;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 waits (bounded: max_polls acquire loads, 256 ns apart at least) until
+// *p >= target; the verdict is shared with the CTA through the shared word `flag`.
+__device__ __forceinline__ bool cta_wait_count(const uint32_t *p, uint32_t target, int *flag,
+                                               uint32_t max_polls = kMaxWaitPolls)
+{
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (uint32_t i = 0; i < max_polls; ++i) {
+            if (ld_acquire(p) >= target) {
+                ok = true;
+                break;
+            }
+            __nanosleep(256);
+        }
+        *flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const bool ok = *flag != 0;
+    __syncthreads();
+    return ok;
 }
 
 // MUFU approximations with flush-to-zero (single SFU instruction each).

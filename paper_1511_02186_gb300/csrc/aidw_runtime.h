@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <vector>
 
 #include "aidw_internal.cuh"
 
@@ -28,11 +29,15 @@ bool dataset_lookup(aidw_ctx *ctx, int64_t id, DatasetDev *dev, double *r_exp);
 int pointer_kind(const void *p, int device);
 int validate_params(const aidw_params *p, int64_t n);
 AlphaMap alpha_map(const aidw_params &p);
+// Shape from `cfg`, or from the context's shape when cfg is null.
 Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bool with_idx,
-               int force_knn_splits, int force_w_splits);
+               int force_knn_splits, int force_w_splits, const aidw_tune_config *cfg = nullptr);
+aidw_tune_config ctx_tune(aidw_ctx *ctx);
+void ctx_set_tune(aidw_ctx *ctx, const aidw_tune_config &c);
 int interpolate_impl(aidw_ctx *ctx, int64_t dsid, const void *qx, const void *qy, int64_t m,
                      const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
-                     cudaStream_t st, int force_knn_splits, int force_w_splits);
+                     cudaStream_t st, int force_knn_splits, int force_w_splits,
+                     const aidw_tune_config *cfg = nullptr);
 int consume_device_error(aidw_ctx *ctx, cudaStream_t st);
 int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
                           const aidw_params &p, const void *qx, const void *qy,
@@ -60,12 +65,23 @@ struct BatchState {
     uint32_t *keys = nullptr, *vals = nullptr, *item_of = nullptr, *perm = nullptr;
     float *sqx = nullptr, *sqy = nullptr;
     void *sort_tmp = nullptr;
+    aidw_tune_config cfg{};  // shape the batch was built with
 };
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
-                BatchState *bs);
+                BatchState *bs, const aidw_tune_config &cfg);
 int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st);
 void batch_release(aidw_ctx *ctx, BatchState *bs, cudaStream_t st);
 // Device bytes one batch item of m queries against n_pad points with k neighbours needs.
-size_t batch_item_bytes(int64_t n_pad, int64_t m, int k);
+size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config &cfg);
 
+}  // namespace aidw
+
+// A prepared batch: its items (kept to rebuild it under another shape) and the built state.
+struct aidw_batch {
+    aidw::BatchState st;
+    std::vector<aidw_batch_item> items;
+};
+
+namespace aidw {
+int batch_prepare(aidw_ctx *ctx, aidw_batch *b, const aidw_tune_config &cfg);
 }  // namespace aidw

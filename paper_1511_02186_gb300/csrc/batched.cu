@@ -36,11 +36,10 @@ using namespace f32dev;
 
 enum UnitType : int32_t { kUnitKnn = 0, kUnitSelect = 1, kUnitWeights = 2, kUnitFinal = 3 };
 
-// Data-split lengths of the batched plan (points). A phase-1 split restarts the neighbour lists,
-// so phase-1 splits are longer.
+// Data-split length of the batched phase-1 plan (points) for datasets too large to prune; a
+// phase-1 split restarts the neighbour lists, so these splits are long. The phase-2 split
+// length is a tuning field (aidw_tune_config.split_points).
 constexpr int64_t kBatchKnnSplit = 262144;
-constexpr int64_t kBatchWSplit = 65536;
-constexpr uint32_t kMaxWaitPolls = 1u << 26;  // x >= 256 ns sleep: tens of seconds at most
 
 struct BatchItemDev {
     DatasetDev ds;
@@ -67,33 +66,6 @@ struct WorkUnit {
     int32_t item, qblock, split, type;
 };
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Thread 0 waits (bounded) until *p >= target; the verdict is shared through `flag`.
-__device__ __forceinline__ bool cta_wait_count(const uint32_t *p, uint32_t target, int *flag)
-{
-    if (threadIdx.x == 0) {
-        bool ok = false;
-        for (uint32_t i = 0; i < kMaxWaitPolls; ++i) {
-            if (ld_acquire(p) >= target) {
-                ok = true;
-                break;
-            }
-            __nanosleep(256);
-        }
-        *flag = ok ? 1 : 0;
-    }
-    __syncthreads();
-    const bool ok = *flag != 0;
-    __syncthreads();
-    return ok;
-}
-
 // Every thread's results are made visible at GPU scope before thread 0 counts the unit done.
 __device__ __forceinline__ void cta_publish(uint32_t *counter)
 {
@@ -103,9 +75,11 @@ __device__ __forceinline__ void cta_publish(uint32_t *counter)
         atomicAdd(counter, 1u);
 }
 
+// QW: phase-2 queries per thread; tw: phase-2 tile points (256 or 512).
+template <int QW>
 __global__ void __launch_bounds__(kThreads, 4)
 f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restrict__ units,
-                 int n_units, uint32_t *next, int *err)
+                 int n_units, uint32_t *next, int *err, int tw)
 {
     extern __shared__ unsigned long long order[];  // tile order of a KNN unit
     __shared__ CullShared cs;
@@ -202,8 +176,15 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.w.q_per_block;
                 const int64_t p0 = static_cast<int64_t>(wu.split) * it.w.split_len;
                 const int64_t p1 = min(p0 + it.w.split_len, it.ds.n_pad);
-                ok = weights_unit<kQW32>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.qparam,
-                                         wu.split, it.part_sum, err, txy, tz, ts);
+                if (tw == 256)
+                    ok = weights_unit<QW, 256>(
+                        it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy, it.qparam, wu.split,
+                        it.part_sum, err, reinterpret_cast<float4(*)[256]>(&txy[0][0]),
+                        reinterpret_cast<float2(*)[256]>(&tz[0][0]), ts);
+                else
+                    ok = weights_unit<QW, kTileF32W>(it.ds, it.m, qbase, p0, p1, it.sqx, it.sqy,
+                                                     it.qparam, wu.split, it.part_sum, err, txy,
+                                                     tz, ts);
                 if (ok)
                     cta_publish(&it.cnt_w[wu.qblock]);
             }
@@ -287,13 +268,25 @@ PassPlan batch_pass(int64_t m, int64_t n_pad, int qpb, int64_t target)
     return pp;
 }
 
-int batch_grid(int sm_count, size_t dyn)
+using BatchKernel = void (*)(const BatchItemDev *, const WorkUnit *, int, uint32_t *, int *,
+                            int);
+
+BatchKernel batch_kernel_for(int qw)
 {
-    cudaFuncSetAttribute(f32_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(dyn));
+    return qw == 2 ? f32_batch_kernel<2> : (qw == 8 ? f32_batch_kernel<8> : f32_batch_kernel<4>);
+}
+
+// Persistent grid: CTAs per SM as occupancy allows, or fewer if the shape asks for it.
+int batch_grid(int sm_count, size_t dyn, int qw, int ctas_per_sm)
+{
+    const BatchKernel fn = batch_kernel_for(qw);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32_batch_kernel, kThreads, dyn);
-    return (n > 0 ? n : 1) * sm_count;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, dyn);
+    n = n > 0 ? n : 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < n)
+        n = ctas_per_sm;
+    return n * sm_count;
 }
 
 }  // namespace
@@ -307,11 +300,12 @@ PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, bool *cull)
     return batch_pass(m, n_pad, qk, *cull ? n_pad : kBatchKnnSplit);
 }
 
-size_t batch_item_bytes(int64_t n_pad, int64_t m, int k)
+size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config &cfg)
 {
     bool cull;
-    const PassPlan pk = batch_knn_plan(m, n_pad, kp_for(k), &cull);
-    const PassPlan pw = batch_pass(m, n_pad, kThreads * kQW32, kBatchWSplit);
+    const PassPlan pk = batch_knn_plan(m, n_pad, kp_for(k, cfg.knn_list), &cull);
+    const PassPlan pw = batch_pass(m, n_pad, kThreads * cfg.queries_per_thread,
+                                   cfg.split_points);
     const size_t mm = static_cast<size_t>(m);
     return align256(pk.splits * static_cast<size_t>(k) * mm * sizeof(float)) +
            align256(mm * sizeof(QParamF32)) + align256(pw.splits * 4 * mm * sizeof(float)) +
@@ -322,8 +316,10 @@ size_t batch_item_bytes(int64_t n_pad, int64_t m, int k)
 
 // Validates the items and builds the device tables of a batch in library memory.
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
-                BatchState *bs)
+                BatchState *bs, const aidw_tune_config &cfg)
 {
+    if (!tune_valid(cfg))
+        return AIDW_ERR_INVALID_ARG;
     if (count < 0 || count > 65535 || (count > 0 && !items))
         return AIDW_ERR_INVALID_ARG;
     const int device = ctx_device(ctx);
@@ -356,12 +352,12 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.out_alpha = b.out_alpha;
         d.m = b.m;
         d.k = b.params.k;
-        d.kp = kp_for(b.params.k);
+        d.kp = kp_for(b.params.k, cfg.knn_list);
         d.r_exp = r_exp;
         d.am = alpha_map(b.params);
         bool cull;
         d.knn = batch_knn_plan(b.m, dev.n_pad, d.kp, &cull);
-        d.w = batch_pass(b.m, dev.n_pad, kThreads * kQW32, kBatchWSplit);
+        d.w = batch_pass(b.m, dev.n_pad, kThreads * cfg.queries_per_thread, cfg.split_points);
         d.ntiles = static_cast<int32_t>(dev.n_pad / kTileF32Knn);
         int p2 = 1;
         while (p2 < d.ntiles)
@@ -450,7 +446,9 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     bs->max_m = max_m;
     bs->dyn_smem = sizeof(unsigned long long) * static_cast<size_t>(std::max(max_p2, 1));
     bs->n_units = static_cast<int>(u.size());
-    bs->grid = batch_grid(ctx_sm_count(ctx), bs->dyn_smem);
+    bs->cfg = cfg;
+    bs->grid = batch_grid(ctx_sm_count(ctx), bs->dyn_smem, cfg.queries_per_thread,
+                          cfg.ctas_per_sm);
     bool ok = true;
     if (count > 0)
         ok &= cudaMemcpyAsync(bs->d_items, h.data(), sizeof(BatchItemDev) * count,
@@ -490,9 +488,9 @@ int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st)
                                                           bs.sqx, bs.sqy, bs.perm);
     if (cudaMemsetAsync(bs.d_counters, 0, bs.counter_bytes, st) != cudaSuccess)
         return AIDW_ERR_CUDA;
-    f32_batch_kernel<<<bs.grid, kThreads, bs.dyn_smem, st>>>(
+    batch_kernel_for(bs.cfg.queries_per_thread)<<<bs.grid, kThreads, bs.dyn_smem, st>>>(
         items, static_cast<const WorkUnit *>(bs.d_units), bs.n_units, bs.d_counters,
-        ctx_err_word(ctx));
+        ctx_err_word(ctx), bs.cfg.tile_points);
     return cudaGetLastError() == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
 }
 
@@ -505,13 +503,65 @@ void batch_release(aidw_ctx *ctx, BatchState *bs, cudaStream_t st)
     bs->block = nullptr;
 }
 
+// (Re)builds a prepared batch under `cfg`: the tables on a private stream, then the query
+// ordering, the counter reset and the persistent kernel captured as one graph. Earlier launches
+// of the batch are waited for first. On failure the batch is rebuilt with its previous shape.
+int batch_prepare(aidw_ctx *ctx, aidw_batch *b, const aidw_tune_config &cfg)
+{
+    if (!tune_valid(cfg))
+        return AIDW_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx_device(ctx)) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    const bool had = b->st.block != nullptr || b->st.graph != nullptr;
+    const aidw_tune_config old = b->st.cfg;
+    if (had) {
+        cudaDeviceSynchronize();
+        batch_release(ctx, &b->st, cap);
+        b->st = BatchState{};
+    }
+    auto attempt = [&](const aidw_tune_config &c) {
+        BatchState fresh;
+        int rc = batch_build(ctx, b->items.data(), static_cast<int32_t>(b->items.size()), cap,
+                             &fresh, c);
+        if (rc == AIDW_OK && cudaStreamSynchronize(cap) != cudaSuccess)
+            rc = AIDW_ERR_CUDA;
+        if (rc == AIDW_OK) {
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const int erc = batch_enqueue(ctx, fresh, cap);
+                ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && erc == AIDW_OK;
+            }
+            ok = ok && cudaGraphInstantiate(&fresh.graph, g, 0) == cudaSuccess;
+            if (g)
+                cudaGraphDestroy(g);
+            if (!ok) {
+                cudaGetLastError();
+                rc = AIDW_ERR_CUDA;
+            }
+        }
+        if (rc != AIDW_OK) {
+            if (fresh.block)
+                batch_release(ctx, &fresh, cap);
+            cudaStreamSynchronize(cap);
+            return rc;
+        }
+        b->st = fresh;
+        return AIDW_OK;
+    };
+    int rc = attempt(cfg);
+    if (rc != AIDW_OK && had)
+        attempt(old);
+    cudaStreamDestroy(cap);
+    return rc;
+}
+
 }  // namespace aidw
 
 using namespace aidw;
-
-struct aidw_batch {
-    BatchState st;
-};
 
 extern "C" {
 
@@ -524,7 +574,7 @@ int aidw_interpolate_batch(aidw_ctx *ctx, const aidw_batch_item *items, int32_t 
         return AIDW_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BatchState bs;
-    int rc = batch_build(ctx, items, count, st, &bs);
+    int rc = batch_build(ctx, items, count, st, &bs, ctx_tune(ctx));
     if (rc)
         return rc;
     rc = batch_enqueue(ctx, bs, st);
@@ -538,41 +588,31 @@ int aidw_batch_create(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count
     if (!ctx || !out)
         return AIDW_ERR_INVALID_ARG;
     *out = nullptr;
-    if (cudaSetDevice(ctx_device(ctx)) != cudaSuccess)
-        return AIDW_ERR_CUDA;
-    cudaStream_t cap;
-    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
-        return AIDW_ERR_CUDA;
+    if (count < 0 || count > 65535 || (count > 0 && !items))
+        return AIDW_ERR_INVALID_ARG;
     aidw_batch *b = new aidw_batch();
-    int rc = batch_build(ctx, items, count, cap, &b->st);
-    if (rc == AIDW_OK && cudaStreamSynchronize(cap) != cudaSuccess)
-        rc = AIDW_ERR_CUDA;
-    if (rc == AIDW_OK) {
-        // Capture the counter reset and the persistent kernel as one graph.
-        cudaGraph_t g = nullptr;
-        bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
-            const int erc = batch_enqueue(ctx, b->st, cap);
-            ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && erc == AIDW_OK;
-        }
-        ok = ok && cudaGraphInstantiate(&b->st.graph, g, 0) == cudaSuccess;
-        if (g)
-            cudaGraphDestroy(g);
-        if (!ok) {
-            cudaGetLastError();
-            rc = AIDW_ERR_CUDA;
-        }
-    }
+    b->items.assign(items, items + count);
+    const int rc = batch_prepare(ctx, b, ctx_tune(ctx));
     if (rc != AIDW_OK) {
-        if (b->st.block)
-            batch_release(ctx, &b->st, cap);
-        cudaStreamSynchronize(cap);
-        cudaStreamDestroy(cap);
         delete b;
         return rc;
     }
-    cudaStreamDestroy(cap);
     *out = b;
+    return AIDW_OK;
+}
+
+int aidw_batch_set_config(aidw_ctx *ctx, aidw_batch *b, const aidw_tune_config *cfg)
+{
+    if (!ctx || !b || !cfg)
+        return AIDW_ERR_INVALID_ARG;
+    return batch_prepare(ctx, b, *cfg);
+}
+
+int aidw_batch_get_config(aidw_ctx *ctx, aidw_batch *b, aidw_tune_config *out)
+{
+    if (!ctx || !b || !out)
+        return AIDW_ERR_INVALID_ARG;
+    *out = b->st.cfg;
     return AIDW_OK;
 }
 

@@ -543,9 +543,10 @@ __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k,
 // run on the MUFU. w = 2^(s (L1 - log2 d2)) with s = alpha/2 and L1 = log2 of the nearest
 // squared distance, i.e. (d1/d)^alpha <= 1: the ratio of Eq. 1 is unchanged and nothing
 // overflows. Each thread sums kChunkW points per query in plain FP32 and merges the chunk sums
-// by Kahan steps; the partial sums of the split go to part_sum[s][0..3][q].
+// by Kahan steps; the partial sums of the split go to part_sum[s][0..3][q]. Tiles of TW points
+// hold whole chunks, so neither Q nor TW changes any query's sequence of operations.
 // ---------------------------------------------------------------------------------------------
-template <int Q>
+template <int Q, int TW>
 __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, int64_t qbase,
                                              int64_t p_begin, int64_t p_end,
                                              const float *__restrict__ qx,
@@ -553,13 +554,14 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
                                              const QParamF32 *qp, int s,
                                              float *__restrict__ part_sum,
                                              int *__restrict__ err,
-                                             float4 (*txy)[kTileF32W],
-                                             float2 (*tz)[kTileF32W], TileSeq &ts)
+                                             float4 (*txy)[TW],
+                                             float2 (*tz)[TW], TileSeq &ts)
 {
     static_assert(Q % 2 == 0, "queries are processed in packed pairs");
+    static_assert(TW % kChunkW == 0 && kPadPoints % TW == 0, "whole chunks, whole tiles");
     constexpr int H = Q / 2;
     const int tid = threadIdx.x;
-    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF32W);
+    const int ntiles = static_cast<int>((p_end - p_begin) / TW);
 
     float2 qxp[H], qyp[H], nsp[H], ccp[H];
     float hw[Q], cw[Q], hz[Q], cz[Q];
@@ -583,12 +585,12 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
     }
     const float2 eps2 = make_float2(kEpsF32, kEpsF32);
 
-    constexpr uint32_t kBxy = kTileF32W * sizeof(float4);
-    constexpr uint32_t kBz = kTileF32W * sizeof(float2);
+    constexpr uint32_t kBxy = TW * sizeof(float4);
+    constexpr uint32_t kBz = TW * sizeof(float2);
     if (tid == 0) {
         for (int t = 0; t < 2 && t < ntiles; ++t) {
             const uint32_t b = (ts.seq + t) & 1;
-            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileF32W;
+            const int64_t o = p_begin + static_cast<int64_t>(t) * TW;
             mbar_arrive_expect_tx(&ts.bar[b], kBxy + kBz);
             tma_load_1d(txy[b], ds.nxy2 + o, kBxy, &ts.bar[b]);
             tma_load_1d(tz[b], ds.zz + o, kBz, &ts.bar[b]);
@@ -607,7 +609,7 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
             ts.seq += ntiles;
             return false;
         }
-        for (int c = 0; c < kTileF32W; c += kChunkW) {
+        for (int c = 0; c < TW; c += kChunkW) {
             float2 sw[H], sz[H];
 #pragma unroll
             for (int h = 0; h < H; ++h)
@@ -639,7 +641,7 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) {
             fence_proxy_async_smem();
-            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileF32W;
+            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * TW;
             mbar_arrive_expect_tx(&ts.bar[b], kBxy + kBz);
             tma_load_1d(txy[b], ds.nxy2 + o, kBxy, &ts.bar[b]);
             tma_load_1d(tz[b], ds.zz + o, kBz, &ts.bar[b]);
@@ -690,13 +692,12 @@ constexpr int knn_q()
     return KP <= 16 ? 4 : 2;
 }
 
-// Register list length for k: the smallest of 8, 12, 16, 32 that holds k.
-__host__ __device__ inline int kp_for(int k)
+// Register list length for k: the smallest of 8, 12, 16, 32 that holds k and kp_min.
+__host__ __device__ inline int kp_for(int k, int kp_min = 0)
 {
-    return k <= 8 ? 8 : (k <= 12 ? 12 : (k <= 16 ? 16 : 32));
+    const int v = k > kp_min ? k : kp_min;
+    return v <= 8 ? 8 : (v <= 12 ? 12 : (v <= 16 ? 16 : 32));
 }
-
-constexpr int kQW32 = 4;  // queries per thread in phase 2 (measured: 4 edges out 6 and 8)
 
 }  // namespace f32dev
 }  // namespace aidw

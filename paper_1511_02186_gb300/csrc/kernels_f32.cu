@@ -59,22 +59,22 @@ f32_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
                               reinterpret_cast<int32_t *>(order + ntiles_p2), cs);
 }
 
-template <int Q>
+template <int Q, int TW>
 __global__ void __launch_bounds__(kThreads)
 f32_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const float *__restrict__ qx,
                    const float *__restrict__ qy, const QParamF32 *__restrict__ qp,
                    float *__restrict__ part_sum, int *__restrict__ err)
 {
-    __shared__ __align__(128) float4 txy[2][kTileF32W];
-    __shared__ __align__(128) float2 tz[2][kTileF32W];
+    __shared__ __align__(128) float4 txy[2][TW];
+    __shared__ __align__(128) float2 tz[2][TW];
     __shared__ __align__(8) uint64_t bar[2];
     init_tile_barriers(bar);
     TileSeq ts{bar, 0u};
     const int s = blockIdx.y;
     const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
-    weights_unit<Q>(ds, m, static_cast<int64_t>(blockIdx.x) * pp.q_per_block, p_begin, p_end,
-                    qx, qy, qp, s, part_sum, err, txy, tz, ts);
+    weights_unit<Q, TW>(ds, m, static_cast<int64_t>(blockIdx.x) * pp.q_per_block, p_begin,
+                        p_end, qx, qy, qp, s, part_sum, err, txy, tz, ts);
 }
 
 __global__ void __launch_bounds__(256)
@@ -147,19 +147,24 @@ int knn_slots_t(bool with_idx)
 
 }  // namespace
 
-int f32_knn_queries_per_block(int k)
+int f32_list_length(int k, int kp_min)
 {
-    return kThreads * (f32dev::kp_for(k) <= 16 ? 4 : 2);
+    return f32dev::kp_for(k, kp_min);
 }
 
-int f32_w_queries_per_block()
+int f32_knn_queries_per_block(int kp)
 {
-    return kThreads * f32dev::kQW32;
+    return kThreads * (kp <= 16 ? 4 : 2);
 }
 
-int f32_knn_slots_per_sm(int k, bool with_idx)
+int f32_w_queries_per_block(int qw)
 {
-    switch (f32dev::kp_for(k)) {
+    return kThreads * qw;
+}
+
+int f32_knn_slots_per_sm(int kp, bool with_idx)
+{
+    switch (kp) {
     case 8: return knn_slots_t<8>(with_idx);
     case 12: return knn_slots_t<12>(with_idx);
     case 16: return knn_slots_t<16>(with_idx);
@@ -167,19 +172,26 @@ int f32_knn_slots_per_sm(int k, bool with_idx)
     }
 }
 
-int f32_w_slots_per_sm()
+template <int Q, int TW>
+int w_slots_t()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32_weights_kernel<f32dev::kQW32>,
-                                                  kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32_weights_kernel<Q, TW>, kThreads, 0);
     return n > 0 ? n : 1;
+}
+
+int f32_w_slots_per_sm(int qw, int tw)
+{
+    if (tw == 256)
+        return qw == 2 ? w_slots_t<2, 256>() : (qw == 8 ? w_slots_t<8, 256>() : w_slots_t<4, 256>());
+    return qw == 2 ? w_slots_t<2, 512>() : (qw == 8 ? w_slots_t<8, 512>() : w_slots_t<4, 512>());
 }
 
 cudaError_t launch_f32_knn(const DatasetDev &ds, const Plan &pl, const float *qx,
                            const float *qy, int k, const Scratch &sc, int *err,
                            cudaStream_t st)
 {
-    switch (f32dev::kp_for(k)) {
+    switch (pl.kp) {
     case 8:
         return pl.with_idx ? launch_knn_t<8, true>(ds, pl, qx, qy, k, sc, err, st)
                            : launch_knn_t<8, false>(ds, pl, qx, qy, k, sc, err, st);
@@ -211,7 +223,7 @@ cudaError_t launch_f32_knn_cull(const DatasetDev &ds, const Plan &pl, const floa
                                 const float *sqy, int k, const Scratch &sc, int *err,
                                 cudaStream_t st)
 {
-    switch (f32dev::kp_for(k)) {
+    switch (pl.kp) {
     case 8:
         return pl.with_idx ? launch_cull_t<8, true>(ds, pl, sqx, sqy, k, sc, err, st)
                            : launch_cull_t<8, false>(ds, pl, sqx, sqy, k, sc, err, st);
@@ -231,9 +243,16 @@ cudaError_t launch_f32_weights(const DatasetDev &ds, const Plan &pl, const float
                                const float *qy, const Scratch &sc, int *err, cudaStream_t st)
 {
     dim3 grid(pl.w.qblocks, pl.w.splits);
-    f32_weights_kernel<f32dev::kQW32><<<grid, kThreads, 0, st>>>(
-        ds, pl.m, pl.w, qx, qy, static_cast<const QParamF32 *>(sc.qparam),
-        static_cast<float *>(sc.part_sum), err);
+    auto fn = f32_weights_kernel<4, 512>;
+    if (pl.tw == 256)
+        fn = pl.qw == 2 ? f32_weights_kernel<2, 256>
+                        : (pl.qw == 8 ? f32_weights_kernel<8, 256> : f32_weights_kernel<4, 256>);
+    else
+        fn = pl.qw == 2 ? f32_weights_kernel<2, 512>
+                        : (pl.qw == 8 ? f32_weights_kernel<8, 512> : f32_weights_kernel<4, 512>);
+    fn<<<grid, kThreads, 0, st>>>(ds, pl.m, pl.w, qx, qy,
+                                  static_cast<const QParamF32 *>(sc.qparam),
+                                  static_cast<float *>(sc.part_sum), err);
     return cudaGetLastError();
 }
 

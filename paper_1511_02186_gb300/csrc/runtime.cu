@@ -70,6 +70,7 @@ struct Flight {
 
 struct ServingRuntime {
     aidw_ctx *ctx = nullptr;
+    aidw_tune_config cfg{};  // kernel shape: the context's when the runtime started
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<int64_t> queue;
@@ -88,9 +89,9 @@ struct ServingRuntime {
 
 namespace {
 
-size_t request_footprint(const Request &r, int64_t n_pad)
+size_t request_footprint(const Request &r, int64_t n_pad, const aidw_tune_config &cfg)
 {
-    size_t b = batch_item_bytes(n_pad, r.m, r.p.k) + 4096;
+    size_t b = batch_item_bytes(n_pad, r.m, r.p.k, cfg) + 4096;
     const size_t m = static_cast<size_t>(r.m);
     if (r.host_qx)
         b += align256(4 * m);
@@ -200,7 +201,7 @@ int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &r
         return AIDW_ERR_CUDA;
     }
     BatchState bs{};
-    rc = batch_build(ctx, items.data(), static_cast<int32_t>(items.size()), st, &bs);
+    rc = batch_build(ctx, items.data(), static_cast<int32_t>(items.size()), st, &bs, rt->cfg);
     if (rc == AIDW_OK)
         rc = batch_enqueue(ctx, bs, st);
     if (rc == AIDW_OK) {
@@ -339,11 +340,13 @@ void worker_main(ServingRuntime *rt)
 ServingRuntime *ensure_serving(aidw_ctx *ctx)
 {
     const size_t left = ctx_budget_left(ctx);
+    const aidw_tune_config cfg = ctx_tune(ctx);
     std::lock_guard<std::mutex> g(ctx_mutex(ctx));
     ServingRuntime *&rt = ctx_serving(ctx);
     if (!rt) {
         rt = new ServingRuntime();
         rt->ctx = ctx;
+        rt->cfg = cfg;
         if (left != SIZE_MAX)
             rt->budget = left / 2;
         cudaSetDevice(ctx_device(ctx));
@@ -402,9 +405,11 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
     ServingRuntime *rt;
     {
         // Create stopped-free runtime with the requested shape.
+        const aidw_tune_config cfg = ctx_tune(ctx);
         std::lock_guard<std::mutex> g(ctx_mutex(ctx));
         rt = new ServingRuntime();
         rt->ctx = ctx;
+        rt->cfg = cfg;
         if (inflight_bytes)
             rt->budget = inflight_bytes;
         if (max_batch_requests)
@@ -466,8 +471,8 @@ int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, 
                 return AIDW_ERR_INVALID_ARG;
         }
     }
-    r.footprint = request_footprint(r, dev.n_pad);
     ServingRuntime *rt = ensure_serving(ctx);
+    r.footprint = request_footprint(r, dev.n_pad, rt->cfg);
     {
         std::lock_guard<std::mutex> g(rt->mu);
         if (rt->queue.size() >= rt->max_queue) {
