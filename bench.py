@@ -328,19 +328,27 @@ def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s
     results["mean_requests_per_launch"] = st.batched_requests / max(1, st.launches)
     results["workload"] = "served_64_datasets_poisson"
 
-    # Unbatched launches of the same request stream (a prefix bounded to about 4e10
-    # pair-evaluations, i.e. a few seconds of FP64 work), one synchronous call per request.
-    prefix, acc = [], 0.0
+    # One set of requests served three ways with nothing else running: one synchronous call per
+    # request in FP64 and in FP32 (unbatched), and all of them submitted at once (batched FP32).
+    # The set: requests of a seeded stream in arrival order, skipping any that would take the
+    # total above 4e10 pair-evaluations (a few seconds of FP64 work), at most 32.
+    subset, acc = [], 0.0
     for _, d, qx, qy in workloads.served_requests(dsw, seed=13, rate=1000.0, duration_s=2.0):
-        if prefix and acc + dsw[d].n * len(qx) > 4e10:
+        pe = float(dsw[d].n * len(qx))
+        if acc + pe > 4e10:
+            continue
+        subset.append((d, qx, qy))
+        acc += pe
+        if len(subset) == 32:
             break
-        prefix.append((d, qx, qy))
-        acc += dsw[d].n * len(qx)
+    cmp = {"requests": len(subset), "pair_evals": acc,
+           "selection": "seeded request stream in arrival order, skipping requests that would "
+                        "take the total above 4e10 pair-evaluations, at most 32"}
     for label, prec in (("unbatched_fp64", aidw.F64), ("unbatched_fp32", aidw.F32C)):
         pp = aidw.default_params(k=10, precision=prec)
         dt = np.float64 if prec == aidw.F64 else np.float32
         reqs = [(d, qx.astype(dt), qy.astype(dt), np.empty(len(qx), dtype=dt))
-                for d, qx, qy in prefix]
+                for d, qx, qy in subset]
         svc = []
         t0 = time.perf_counter()
         for d, qx, qy, out in reqs:
@@ -349,12 +357,26 @@ def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s
             svc.append(time.perf_counter() - t1)
         wall = time.perf_counter() - t0
         svc_ms = np.array(svc) * 1e3
-        results[label] = {"requests": len(reqs), "pair_evals": acc,
-                          "throughput": acc / wall, "unit": UNIT,
-                          "p50_service_ms": float(np.percentile(svc_ms, 50)),
-                          "p99_service_ms": float(np.percentile(svc_ms, 99)),
-                          "launch": "one aidw_interpolate per request, host arrays, "
-                                    "back to back"}
+        cmp[label] = {"throughput": acc / wall, "unit": UNIT, "wall_s": wall,
+                      "p50_service_ms": float(np.percentile(svc_ms, 50)),
+                      "p99_service_ms": float(np.percentile(svc_ms, 99)),
+                      "launch": "one aidw_interpolate per request, host arrays, back to back"}
+    reqs = [(d, qx.astype(np.float32), qy.astype(np.float32), np.empty(len(qx), np.float32))
+            for d, qx, qy in subset]
+    t0 = time.perf_counter()
+    ids = [ctx.submit(handles[d], qx, qy, p, out)[1] for d, qx, qy, out in reqs]
+    for rid in ids:
+        ctx.wait(rid, -1)
+    wall = time.perf_counter() - t0
+    lat = np.array([ctx.latency_us(rid) for rid in ids]) / 1e3
+    for rid in ids:
+        ctx.release(rid)
+    cmp["batched_fp32_burst"] = {"throughput": acc / wall, "unit": UNIT, "wall_s": wall,
+                                 "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)),
+                                 "launch": "all requests submitted at once to the serving "
+                                           "runtime (continuous batching)"}
+    results["same_requests_batched_vs_unbatched"] = cmp
     for h in handles:
         h.destroy()
     return results
