@@ -145,6 +145,25 @@ int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int
 int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, const float *qy,
                              int64_t m, const aidw_params *p, float *out, void *stream);
 
+/* ---- the paper's kernel designs, for comparison ------------------------------------------ */
+/* AIDW computed by the paper's own GPU designs (Sec. 3.1), rebuilt for sm_103a as a measured
+ * comparison beside aidw_interpolate: one thread per query scanning all n points twice (phase 1
+ * keeps the k smallest squared distances, Sec. 3.1.2; phase 2 forms the weights of Eq. 1), with
+ * version AIDW_VERSION_NAIVE (every data point read from global memory) or AIDW_VERSION_TILED
+ * (blocks of 256 data points staged in shared memory for the thread block, Sec. 3.1.1), and the
+ * data in layout AIDW_LAYOUT_SOA (x[], y[], z[]) or AIDW_LAYOUT_AOAS ({x, y, z, 0} aligned
+ * structures, Sec. 3.1.3), copied from the dataset in the caller's order for the call. Precision
+ * as p->precision (float or double arrays). Per pair the arithmetic is aidw_interpolate's, so
+ * the four variants of one precision give identical results. Device arrays only; stream-ordered.
+ * Errors: INVALID_ARG (bad version, layout, size or a host array), NOT_FOUND, OOM. */
+#define AIDW_VERSION_NAIVE 0
+#define AIDW_VERSION_TILED 1
+#define AIDW_LAYOUT_SOA 0
+#define AIDW_LAYOUT_AOAS 1
+int aidw_interpolate_paper(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy,
+                           int64_t m, const aidw_params *p, void *out, float *out_alpha,
+                           int32_t version, int32_t layout, void *stream);
+
 /* ---- batched launch (many datasets in one persistent kernel) -------------------------- */
 /* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays of the context's
  * device, float) and its parameters (precision must be AIDW_F32C; k and levels may differ per

@@ -31,6 +31,10 @@ F64 = 1
 DTYPE_F32 = 0
 DTYPE_F64 = 1
 MAX_K = 32
+VERSION_NAIVE = 0
+VERSION_TILED = 1
+LAYOUT_SOA = 0
+LAYOUT_AOAS = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -133,6 +137,8 @@ SIGNATURES = {
     "aidw_measure_pipe_rates": (ctypes.c_int, [_P, _P]),
     "aidw_debug_fail_alloc_after": (ctypes.c_int, [_P, _I64]),
     "aidw_debug_expire_wait": (ctypes.c_int, [_P, _I32, ctypes.c_uint32]),
+    "aidw_interpolate_paper": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _I32, _I32,
+                                              _P]),
     "aidw_tune_config_default": (ctypes.c_int, [_P]),
     "aidw_tune_config_check": (ctypes.c_int, [_P]),
     "aidw_set_tune_config": (ctypes.c_int, [_P, _P]),
@@ -410,6 +416,28 @@ class Context:
             if keep is not None and keep is not res and isinstance(res, np.ndarray):
                 res[...] = keep
         return out, out_alpha, out_knn
+
+    def interpolate_paper(self, ds: Dataset, qx, qy, params: Params | None = None,
+                          version: int = VERSION_TILED, layout: int = LAYOUT_SOA, out=None,
+                          out_alpha=None, want_alpha=False, stream=None):
+        """AIDW by the paper's naive / tiled kernel design with SoA / AoaS data (CUDA
+        tensors); returns (out, out_alpha or None)."""
+        p = params or default_params()
+        fdt = "f8" if p.precision == F64 else "f4"
+        kqx, pqx = _prep(qx, fdt)
+        kqy, pqy = _prep(qy, fdt)
+        m = int(kqx.shape[0])
+        if out is None:
+            out = _out_like(qx, (m,), fdt)
+        if want_alpha and out_alpha is None:
+            out_alpha = _out_like(qx, (m,), "f4")
+        po = _prep_out(out, fdt)
+        pa = None if out_alpha is None else _prep_out(out_alpha, "f4")
+        _check(self.lib.aidw_interpolate_paper(self.ptr, ds.handle, pqx, pqy, m,
+                                               ctypes.byref(p), po, pa, int(version),
+                                               int(layout), _stream_of(qx, stream)),
+               "aidw_interpolate_paper")
+        return out, out_alpha
 
     def idw(self, ds: Dataset, qx, qy, alpha: float, precision: int = F32C, out=None,
             stream=None):
