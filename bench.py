@@ -382,31 +382,30 @@ def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s
     return results
 
 
-def bench_paper_designs(ctx, dev, stream, n: int = 262144, q64: int = 4096):
+def bench_paper_designs(ctx, dev, stream, n: int = 262144, n64: int = 32768):
     """The paper's kernel designs (naive / tiled x SoA / AoaS, Sec. 3.1) against the optimized
-    path on one uniform workload (n = m = 262,144 in [0,1000]^2, k = 10): FP32 over all queries,
-    FP64 on a seeded sample of q64 queries. Each variant runs once on 1,024 queries (warm-up),
-    then once timed."""
+    path on uniform workloads in [0,1000]^2 with k = 10 and m = 262,144 queries (enough
+    one-thread-per-query blocks to fill every SM): FP32 with n = 262,144 data points, FP64 with
+    n64 = 32,768. Each variant runs once on 1,024 queries (warm-up), then once timed."""
     import torch
     from paper_1511_02186_gb300 import aidw, workloads
-    wl = workloads.uniform_paper(0, n=n, m=n)
-    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    res = {"workload": f"uniform_{n}x{n}", "n": n, "m": n, "k": wl.k}
+    res = {}
     names = {(aidw.VERSION_NAIVE, aidw.LAYOUT_SOA): "naive_soa",
              (aidw.VERSION_NAIVE, aidw.LAYOUT_AOAS): "naive_aoas",
              (aidw.VERSION_TILED, aidw.LAYOUT_SOA): "tiled_soa",
              (aidw.VERSION_TILED, aidw.LAYOUT_AOAS): "tiled_aoas"}
-    idx = np.random.default_rng(41).choice(wl.m, q64, replace=False)
-    for prec, label, sel in ((aidw.F32C, "fp32", None), (aidw.F64, "fp64", idx)):
+    for prec, label, nd in ((aidw.F32C, "fp32", n), (aidw.F64, "fp64", n64)):
+        wl = workloads.uniform_paper(0, n=nd, m=n)
+        ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
         dt = torch.float64 if prec == aidw.F64 else torch.float32
-        qxa, qya = (wl.qx, wl.qy) if sel is None else (wl.qx[sel], wl.qy[sel])
-        qx = torch.as_tensor(qxa, dtype=dt, device=dev)
-        qy = torch.as_tensor(qya, dtype=dt, device=dev)
-        out = torch.empty(len(qxa), dtype=dt, device=dev)
+        qx = torch.as_tensor(wl.qx, dtype=dt, device=dev)
+        qy = torch.as_tensor(wl.qy, dtype=dt, device=dev)
+        out = torch.empty(wl.m, dtype=dt, device=dev)
         p = aidw.default_params(k=wl.k, levels=wl.levels, precision=prec)
-        pairs = float(len(qxa)) * n
-        row = {"pair_evals": pairs}
+        pairs = float(wl.m) * wl.n
+        row = {"workload": f"uniform_{wl.n}x{wl.m}", "n": wl.n, "m": wl.m, "k": wl.k,
+               "pair_evals": pairs}
 
         def timed(fn):
             fn(qx[:1024], qy[:1024], out[:1024])
@@ -424,12 +423,11 @@ def bench_paper_designs(ctx, dev, stream, n: int = 262144, q64: int = 4096):
         row["optimized"] = timed(lambda a, b, o: ctx.interpolate(
             ds, a, b, p, out=o, stream=stream.cuda_stream))
         row["tiled_over_naive_soa"] = row["naive_soa"]["ms"] / row["tiled_soa"]["ms"]
+        row["soa_over_aoas_naive"] = row["naive_aoas"]["ms"] / row["naive_soa"]["ms"]
         row["soa_over_aoas_tiled"] = row["tiled_aoas"]["ms"] / row["tiled_soa"]["ms"]
         row["optimized_over_tiled_soa"] = row["tiled_soa"]["ms"] / row["optimized"]["ms"]
-        if sel is not None:
-            row["sample"] = f"{q64} seeded queries x all {n} data points"
         res[label] = row
-    ds.destroy()
+        ds.destroy()
     return res
 
 

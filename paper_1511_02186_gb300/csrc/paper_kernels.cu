@@ -40,6 +40,13 @@ struct Num<float> {
     __device__ static float sqrt(float a) { return __fsqrt_rn(a); }
     __device__ static float lg2(float a) { return lg2_approx(a); }
     __device__ static float ex2(float a) { return ex2_approx(a); }
+    // Hides a value from the compiler so that lg2 of it runs on the MUFU like the per-pair lg2
+    // (a compile-time lg2 of a constant need not equal the MUFU result).
+    __device__ static float opaque(float a)
+    {
+        asm volatile("" : "+f"(a));
+        return a;
+    }
 };
 
 template <>
@@ -53,6 +60,11 @@ struct Num<double> {
     __device__ static double sqrt(double a) { return __dsqrt_rn(a); }
     __device__ static double lg2(double a) { return log2(a); }
     __device__ static double ex2(double a) { return exp2(a); }
+    __device__ static double opaque(double a)
+    {
+        asm volatile("" : "+d"(a));
+        return a;
+    }
 };
 
 // The caller-order copies of one dataset in the layout under test.
@@ -177,15 +189,18 @@ paper_aidw_kernel(Layout<T> d, const T *__restrict__ qx, const T *__restrict__ q
     const double R = r_obs / r_exp;           // Eq. 4
     const double mu = membership_eq5(R, am);  // Eq. 5
     const double alpha = alpha_eq6(mu, am);   // Eq. 6
+    // L1 = log2(d1^2 + eps) through the same instruction as every pair's log2, so that a
+    // coincident point (d2 == eps) gets exactly e = 0.
+    const T L1 = N::lg2(N::opaque(N::add(d1, N::kEps)));
     T neg_s, c;
     if (d1 == T(0)) {
         // Coincident query: weight 1 on every coincident point, 0 elsewhere.
         neg_s = -N::kCoinc;
-        c = N::kCoinc * N::lg2(N::kEps);
+        c = N::kCoinc * L1;
     } else {
         const T sh = static_cast<T>(0.5 * alpha);
         neg_s = -sh;
-        c = sh * N::lg2(N::add(d1, N::kEps));
+        c = sh * L1;
     }
 
     // ---- phase 2: Eq. 1 over all points ----
