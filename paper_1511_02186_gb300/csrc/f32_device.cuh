@@ -349,7 +349,13 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
     }
     __syncthreads();
     const float4 qb = cs.box;
-    // Lower bounds of the box-to-box squared distance, keyed for an ascending sort.
+    const float qcx = 0.5f * (qb.x + qb.z), qcy = 0.5f * (qb.y + qb.w);
+    // Lower bounds of the box-to-box squared distance, keyed for an ascending sort; among tiles
+    // with equal bounds (in particular every tile that overlaps the query box, bound 0) the one
+    // whose centre is nearest the query box's centre comes first, so the lists fill with near
+    // points early and later tiles rarely insert. Key: bound (32 bits), centre distance
+    // (the top 19 bits of its FP32 encoding), tile (13 bits).
+    static_assert(kMaxCullTiles <= 8192, "13-bit tile field");
     for (int t = tid; t < ntiles_p2; t += kThreads) {
         unsigned long long key = ~0ull;
         if (t < ntiles) {
@@ -357,7 +363,10 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
             const float dx = fmaxf(0.0f, fmaxf(tb.x - qb.z, qb.x - tb.z));
             const float dy = fmaxf(0.0f, fmaxf(tb.y - qb.w, qb.y - tb.w));
             const float lb = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), kBoundShrink);
+            const float cx = 0.5f * (tb.x + tb.z) - qcx, cy = 0.5f * (tb.y + tb.w) - qcy;
+            const float cd = fminf(fmaf(cx, cx, cy * cy), 3.0e38f);  // finite, >= 0
             key = (static_cast<unsigned long long>(__float_as_uint(lb)) << 32) |
+                  (static_cast<unsigned long long>(__float_as_uint(cd) >> 13) << 13) |
                   static_cast<unsigned long long>(t);
         }
         order[t] = key;
@@ -384,7 +393,7 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
     if (tid == 0) {
         int issued = 0;
         for (; issued < 2 && issued < ntiles; ++issued) {
-            const int64_t t = static_cast<int64_t>(order[issued] & 0xffffffffull);
+            const int64_t t = static_cast<int64_t>(order[issued] & 0x1fffull);
             const uint32_t b = (ts.seq + issued) & 1;
             mbar_arrive_expect_tx(&ts.bar[b], kBytes);
             tma_load_1d(tile[b], ds.nxy2 + t * kTileF32Knn, kBytes, &ts.bar[b]);
@@ -405,7 +414,7 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
             ok = false;
             break;
         }
-        const int64_t t = static_cast<int64_t>(key & 0xffffffffull);
+        const int64_t t = static_cast<int64_t>(key & 0x1fffull);
         knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem);
         float mx = -CUDART_INF_F;
 #pragma unroll
@@ -424,7 +433,7 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
             const int nx = i + 2;
             if (nx < ntiles &&
                 __uint_as_float(static_cast<uint32_t>(order[nx] >> 32)) <= v) {
-                const int64_t tn = static_cast<int64_t>(order[nx] & 0xffffffffull);
+                const int64_t tn = static_cast<int64_t>(order[nx] & 0x1fffull);
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&ts.bar[b], kBytes);
                 tma_load_1d(tile[b], ds.nxy2 + tn * kTileF32Knn, kBytes, &ts.bar[b]);
