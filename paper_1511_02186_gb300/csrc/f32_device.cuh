@@ -296,9 +296,11 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
     float2 qxp[H], qyp[H], nthr[H];
     float L[Q][KP];
     float bx0 = CUDART_INF_F, by0 = CUDART_INF_F, bx1 = -CUDART_INF_F, by1 = -CUDART_INF_F;
+    // Each warp takes 32 Q consecutive Z-ordered queries, so its queries have a compact box.
+    const int64_t wbase = qbase + static_cast<int64_t>(warp) * 32 * Q + lane;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        const int64_t q = min(wbase + j * 32, m - 1);
         const float a = sqx[q], b = sqy[q];
         bx0 = fminf(bx0, a);
         by0 = fminf(by0, b);
@@ -329,6 +331,8 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
         bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
         by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
     }
+    const float4 wb = make_float4(bx0, by0, bx1, by1);  // the warp's query box
+    float wthr = CUDART_INF_F;                          // the warp's largest k-th distance
     if (lane == 0) {
         red[0][warp] = bx0;
         red[1][warp] = by0;
@@ -415,13 +419,21 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
             break;
         }
         const int64_t t = static_cast<int64_t>(key & 0x1fffull);
-        knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem);
+        // A warp skips a tile that cannot reach any of its queries: the same bound as the
+        // block's, from the warp's own box against its own k-th distances (warp-uniform).
+        const float4 tb = ds.tile_box[t];
+        const float wdx = fmaxf(0.0f, fmaxf(tb.x - wb.z, wb.x - tb.z));
+        const float wdy = fmaxf(0.0f, fmaxf(tb.y - wb.w, wb.y - tb.w));
+        const float wlb = __fmul_rn(__fmaf_rn(wdx, wdx, __fmul_rn(wdy, wdy)), kBoundShrink);
+        if (!(wlb > wthr))
+            knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem);
         float mx = -CUDART_INF_F;
 #pragma unroll
         for (int j = 0; j < Q; ++j)
             mx = fmaxf(mx, L[j][KP - 1]);
         for (int o = 16; o > 0; o >>= 1)
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        wthr = mx;
         if (lane == 0)
             red[0][warp] = mx;
         __syncthreads();
@@ -458,7 +470,7 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
         return false;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const int64_t q = qbase + j * kThreads + tid;
+        const int64_t q = wbase + j * 32;
         if (q >= m)
             continue;
 #pragma unroll
