@@ -635,7 +635,9 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
 #pragma unroll
             for (int h = 0; h < H; ++h)
                 sw[h] = sz[h] = make_float2(0.0f, 0.0f);
-#pragma unroll 4
+            // The whole chunk unrolled (measured: 355 ms at 1M x 1M against 357-359 ms for
+            // steps of 4, 8 or 16 points, with 70 registers instead of 80).
+#pragma unroll
             for (int u = 0; u < kChunkW; ++u) {
                 const float4 p = txy[b][c + u];
                 const float2 zz = tz[b][c + u];
