@@ -420,8 +420,14 @@ def bench_paper_designs(ctx, dev, stream, n: int = 262144, n64: int = 32768):
         for (ver, lay), nm in names.items():
             row[nm] = timed(lambda a, b, o, ver=ver, lay=lay: ctx.interpolate_paper(
                 ds, a, b, p, version=ver, layout=lay, out=o, stream=stream.cuda_stream))
+        ctx.set_profiling(True)
         row["optimized"] = timed(lambda a, b, o: ctx.interpolate(
             ds, a, b, p, out=o, stream=stream.cuda_stream))
+        kt = ctx.kernel_times()
+        ctx.set_profiling(False)
+        row["optimized"]["kernel_ms"] = {"knn": kt.knn_ms, "select": kt.select_ms,
+                                         "weights": kt.weights_ms, "finalize": kt.finalize_ms,
+                                         "knn_splits": kt.splits, "w_splits": kt.weight_splits}
         row["tiled_over_naive_soa"] = row["naive_soa"]["ms"] / row["tiled_soa"]["ms"]
         row["soa_over_aoas_naive"] = row["naive_aoas"]["ms"] / row["naive_soa"]["ms"]
         row["soa_over_aoas_tiled"] = row["tiled_aoas"]["ms"] / row["tiled_soa"]["ms"]

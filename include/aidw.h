@@ -153,8 +153,10 @@ int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, co
  * (blocks of 256 data points staged in shared memory for the thread block, Sec. 3.1.1), and the
  * data in layout AIDW_LAYOUT_SOA (x[], y[], z[]) or AIDW_LAYOUT_AOAS ({x, y, z, 0} aligned
  * structures, Sec. 3.1.3), copied from the dataset in the caller's order for the call. Precision
- * as p->precision (float or double arrays). Per pair the arithmetic is aidw_interpolate's, so
- * the four variants of one precision give identical results. Device arrays only; stream-ordered.
+ * as p->precision (float or double arrays). Per pair the FP32 arithmetic is aidw_interpolate's;
+ * in FP64 the weights use the CUDA library's log2 / exp2 (aidw_interpolate's FP64 path has its
+ * own table-driven pair). The four variants of one precision give identical results. Device
+ * arrays only; stream-ordered.
  * Errors: INVALID_ARG (bad version, layout, size or a host array), NOT_FOUND, OOM. */
 #define AIDW_VERSION_NAIVE 0
 #define AIDW_VERSION_TILED 1

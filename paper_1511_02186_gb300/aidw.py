@@ -159,6 +159,7 @@ SIGNATURES = {
 DEBUG_SIGNATURES = {
     "aidw_debug_interpolate_splits": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P,
                                                      _I32, _I32]),
+    "aidw_debug_f64_log2_exp2": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
 }
 
 

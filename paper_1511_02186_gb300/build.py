@@ -36,7 +36,8 @@ def _sources():
 
 def _deps():
     return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
-        glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(ROOT, "include", "aidw.h")]
+        glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(CSRC, "*.inc"))) + [
+            os.path.join(ROOT, "include", "aidw.h")]
 
 
 def up_to_date() -> bool:

@@ -6,6 +6,7 @@
 #include <math_constants.h>
 
 #include "aidw_internal.cuh"
+#include "f64_math.cuh"
 
 namespace aidw {
 namespace {
@@ -226,11 +227,11 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     QParamF64 o;
     if (d1 == 0.0) {
         o.neg_s = -kCoincScaleF64;
-        o.c = kCoincScaleF64 * log2(kEpsF64);
+        o.c = kCoincScaleF64 * f64math::log2_c(kEpsF64);
     } else {
         const double sh = 0.5 * alpha;
         o.neg_s = -sh;
-        o.c = sh * log2(__dadd_rn(d1, kEpsF64));
+        o.c = sh * f64math::log2_c(__dadd_rn(d1, kEpsF64));
     }
     qp[q] = o;
     if (out_alpha)
@@ -246,9 +247,11 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
     __shared__ __align__(128) double2 txy[2][kTileF64W];
     __shared__ __align__(128) double tz[2][kTileF64W];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ f64math::Tables tabs;
 
     const int tid = threadIdx.x;
     const int s = blockIdx.y;
+    f64math::load_tables(tabs);  // ordered before use by the barrier after the mbarrier set-up
     const int64_t qbase = static_cast<int64_t>(blockIdx.x) * pp.q_per_block;
     const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
@@ -305,7 +308,8 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
                     const double d2 = dist2_eps(qxr[j], qyr[j], p.x, p.y);
-                    const double w = exp2(__fma_rn(log2(d2), ns[j], cc[j]));
+                    const double w = f64math::exp2_t(
+                        __fma_rn(f64math::log2_t(d2, tabs), ns[j], cc[j]), tabs);
                     sw[j] = __dadd_rn(sw[j], w);
                     sz[j] = __fma_rn(w, pz, sz[j]);
                 }
@@ -475,3 +479,34 @@ cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
 }
 
 }  // namespace aidw
+
+// Test hook: the FP64 path's log2 and exp2 evaluated elementwise on device arrays.
+namespace aidw {
+namespace {
+__global__ void f64_math_probe_kernel(const double *__restrict__ x, const double *__restrict__ y,
+                                      int64_t n, double *__restrict__ lx,
+                                      double *__restrict__ ey)
+{
+    __shared__ f64math::Tables tabs;
+    f64math::load_tables(tabs);
+    __syncthreads();
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        lx[i] = f64math::log2_t(x[i], tabs);
+        ey[i] = f64math::exp2_t(y[i], tabs);
+    }
+}
+}  // namespace
+}  // namespace aidw
+
+extern "C" int aidw_debug_f64_log2_exp2(const double *x, const double *y, int64_t n, double *lx,
+                                        double *ey)
+{
+    if (n < 0 || (n > 0 && (!x || !y || !lx || !ey)))
+        return AIDW_ERR_INVALID_ARG;
+    if (n == 0)
+        return AIDW_OK;
+    const unsigned blocks = static_cast<unsigned>(n < 256 * 1024 ? (n + 255) / 256 : 1024);
+    aidw::f64_math_probe_kernel<<<blocks, 256>>>(x, y, n, lx, ey);
+    return cudaDeviceSynchronize() == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
+}

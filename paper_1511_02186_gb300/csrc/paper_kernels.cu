@@ -7,8 +7,9 @@
 // for r_obs (Eq. 3), phase 2 forms the weights of Eq. 1 over all points.
 //
 // The arithmetic per pair is the optimized path's (weights normalised by the nearest distance
-// through log2 / exp2, chunk sums merged by compensated steps), so the four variants of one
-// precision produce the same bits and the comparison isolates data layout and tiling.
+// through log2 / exp2, chunk sums merged by compensated steps; in FP64 with the CUDA library's
+// log2 / exp2 where the optimized path has its own table-driven pair), so the four variants of
+// one precision produce the same bits and the comparison isolates data layout and tiling.
 #include <math_constants.h>
 
 #include <algorithm>

@@ -161,3 +161,39 @@ def test_batch_edge_cases(ctx):
         ctx.interpolate_batch([(ds, qx, qx, aidw.default_params(k=3, precision=aidw.F64),
                                 torch.empty(10, dtype=torch.float32, device="cuda"), None)])
     ds.destroy()
+
+
+def test_full_size_batched_workload_sampled(ctx):
+    """The benchmark's 256-dataset batch, prepared and autotuned as bench.py times it: 16
+    seeded queries of every item against the oracle (every query of small items is still in the
+    batch), plus the invariants on all outputs (finite, within [min z, max z])."""
+    import torch
+    wls = workloads.batched(0)
+    items = []
+    for wl in wls:
+        ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+        qx = torch.as_tensor(wl.qx, dtype=torch.float32, device="cuda")
+        qy = torch.as_tensor(wl.qy, dtype=torch.float32, device="cuda")
+        out = torch.full((wl.m,), float("nan"), dtype=torch.float32, device="cuda")
+        items.append((ds, qx, qy, aidw.default_params(k=wl.k), out, None))
+    pb = ctx.batch_create(items)
+    pb.autotune(reps=1)
+    for it in items:
+        it[4].fill_(float("nan"))
+    pb.launch()
+    torch.cuda.synchronize()
+    assert ctx.check_device_errors() == aidw.OK
+    rng = np.random.default_rng(77)
+    worst = 0.0
+    for wl, it in zip(wls, items):
+        z = it[4].cpu().numpy().astype(np.float64)
+        src = wl.as_f32()
+        assert np.isfinite(z).all()
+        assert z.min() >= src.z.min() - 1e-5 and z.max() <= src.z.max() + 1e-5
+        idx = rng.choice(wl.m, 16, replace=False)
+        ref, _ = oracle_for(wl, aidw.F32C, q_idx=idx)
+        worst = max(worst, rel_err(z[idx], ref).max())
+    assert worst <= TOL_F32, worst
+    pb.destroy()
+    for it in items:
+        it[0].destroy()

@@ -1,0 +1,78 @@
+"""The FP64 path's table-driven log2 / exp2 against error bounds, evaluated on the GPU through
+the library's probe hook: log2 within 2 ulps of max(1, |log2 x|) in absolute terms (the
+accuracy the weights of Eq. 1 need: log2 is scaled by alpha/2 and exponentiated), exp2 within
+4 ulps relative, exact at the points the coincidence rule relies on (log2 of the smallest
+normal double, exp2(0)), and the limits the scan relies on (log2(+inf) = +inf, exp2 of very
+negative arguments = 0). References: numpy's log2 / exp2 (within an ulp), checked on a subset
+with 120-bit arithmetic."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1511_02186_gb300 import aidw
+
+pytestmark = pytest.mark.gpu
+
+DBL_MIN = np.finfo(np.float64).tiny
+ULP1 = 2.0 ** -52
+
+
+def probe(x, y):
+    import torch
+    lib = aidw.load()
+    tx = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    ty = torch.as_tensor(y, dtype=torch.float64, device="cuda")
+    lx = torch.empty_like(tx)
+    ey = torch.empty_like(ty)
+    rc = lib.aidw_debug_f64_log2_exp2(ctypes.c_void_p(tx.data_ptr()),
+                                      ctypes.c_void_p(ty.data_ptr()), int(tx.numel()),
+                                      ctypes.c_void_p(lx.data_ptr()),
+                                      ctypes.c_void_p(ey.data_ptr()))
+    assert rc == aidw.OK
+    return lx.cpu().numpy(), ey.cpu().numpy()
+
+
+def test_log2_exp2_error_bounds():
+    rng = np.random.default_rng(3)
+    n = 1 << 20
+    x = np.exp(rng.uniform(np.log(DBL_MIN), np.log(1e300), n))
+    x[:4096] = 1.0 + rng.uniform(-1e-3, 1e-3, 4096)          # near 1: log2 near 0
+    x[4096:8192] = 2.0 ** rng.integers(-1022, 1000, 4096)     # powers of two: exact results
+    y = rng.uniform(-1020.9, 8.0, n)
+    y[:4096] = rng.uniform(-1e-3, 1e-3, 4096)
+    lx, ey = probe(x, y)
+    ref_l = np.log2(x)
+    err_l = np.abs(lx - ref_l) / np.maximum(1.0, np.abs(ref_l))
+    assert err_l.max() <= 2 * ULP1, err_l.max()
+    assert np.array_equal(lx[4096:8192], ref_l[4096:8192])   # exact on powers of two
+    ref_e = np.exp2(y)
+    err_e = np.abs(ey / ref_e - 1.0)
+    assert err_e.max() <= 4 * ULP1 / 2, err_e.max()
+
+
+def test_against_high_precision_subset():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 120
+    rng = np.random.default_rng(4)
+    x = np.exp(rng.uniform(np.log(DBL_MIN), np.log(1e300), 512))
+    y = rng.uniform(-1020.9, 4.0, 512)
+    lx, ey = probe(x, y)
+    for a, v in zip(x, lx):
+        t = mp.log(mp.mpf(float(a)), 2)
+        assert abs(mp.mpf(float(v)) - t) <= 2 * ULP1 * max(1, abs(t))
+    for b, v in zip(y, ey):
+        t = mp.power(2, mp.mpf(float(b)))
+        assert abs(mp.mpf(float(v)) / t - 1) <= 2 * ULP1
+
+
+def test_special_values():
+    x = np.array([DBL_MIN, 1.0, 2.0, 0.5, np.inf, 1e308, 3.0])
+    y = np.array([0.0, -1.0, 1.0, -1021.0, -1e300, -np.inf, -1020.5])
+    lx, ey = probe(x, y)
+    assert lx[0] == -1022.0 and lx[1] == 0.0 and lx[2] == 1.0 and lx[3] == -1.0
+    assert np.isposinf(lx[4])
+    assert abs(lx[5] - np.log2(1e308)) <= 2 * ULP1 * np.log2(1e308)
+    assert ey[0] == 1.0 and ey[1] == 0.5 and ey[2] == 2.0
+    assert ey[3] == 0.0 and ey[4] == 0.0 and ey[5] == 0.0
+    assert ey[6] > 0.0 and abs(ey[6] / np.exp2(-1020.5) - 1) <= 2 * ULP1

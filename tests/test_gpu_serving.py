@@ -172,3 +172,35 @@ def test_submit_rejects_bad_requests():
         assert ctx.submit(ds, q, q, aidw.default_params(k=3), out)[0] in (
             aidw.ERR_NOT_FOUND, aidw.ERR_INVALID_ARG)
         time.sleep(0.01)
+
+
+def test_full_size_served_workload_sampled():
+    """Requests of the benchmark's served workload (64 resident datasets of 16K-1M points,
+    256-262,144 host-array queries each), submitted as a burst: 16 seeded queries of each of
+    the first 24 requests against the oracle, and every output finite."""
+    with aidw.Context(0) as ctx:
+        dsw = workloads.served_datasets(0)
+        handles = [ctx.create_dataset(w.x, w.y, w.z, w.area) for w in dsw]
+        p = aidw.default_params(k=10)
+        reqs = workloads.served_requests(dsw, seed=12, rate=200.0, duration_s=1.0)[:24]
+        subs = []
+        for _, d, qx, qy in reqs:
+            out = np.full(len(qx), np.nan, dtype=np.float32)
+            q32x, q32y = qx.astype(np.float32), qy.astype(np.float32)
+            rc, rid = ctx.submit(handles[d], q32x, q32y, p, out)
+            assert rc == aidw.OK
+            subs.append((d, qx, qy, out, rid))
+        rng = np.random.default_rng(5)
+        worst = 0.0
+        for d, qx, qy, out, rid in subs:
+            assert ctx.wait(rid, 120_000_000) == aidw.OK
+            assert np.isfinite(out).all()
+            w = dsw[d]
+            wl = workloads.Workload(w.name, w.x, w.y, w.z, w.area, qx, qy, k=10)
+            idx = rng.choice(len(qx), min(16, len(qx)), replace=False)
+            ref, _ = oracle_for(wl, aidw.F32C, q_idx=idx)
+            worst = max(worst, rel_err(out[idx], ref).max())
+            ctx.release(rid)
+        assert worst <= TOL_F32, worst
+        st = ctx.serving_stats()
+        assert st.completed == len(subs) and st.failed == 0
