@@ -271,6 +271,7 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     // A split restarts its neighbour lists: about k (1 + ln(n_split / k)) insertions per query,
     // each a rescan of a chunk by a partly idle warp. Measured on GB300 at n = m = 2^20,
     // k = 10, every extra split costs about as much as scanning 100,000 more points.
+    pl.knn_slots = ks * ctx->sm_count;
     pl.knn = plan_pass(m, n_pad, qk, ks * ctx->sm_count, 10000 * k);
     pl.w = plan_pass(m, n_pad, qw, ws * ctx->sm_count, 1024);
     const int64_t G = n_pad / kPadPoints;
@@ -411,51 +412,90 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
 // more than it saves).
 constexpr int64_t kCullMinQueries = 2048;
 
-bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m)
+// The pruned phase 1 serves FP32 calls, and FP64 calls that do not ask for the neighbour
+// indices (the FP64 index lists keep the oracle's tie order, which needs the caller-order scan),
+// when there are enough queries: with m queries spread over the data, a block of q queries
+// covers about q/m of the area, so each of the m/q blocks visits about n q / (512 m) tiles, and
+// with fewer blocks than the GPU holds (P) the pruned scan takes about n q^2 P / m per-pair
+// steps of one CTA against n m / P steps of each CTA for the split scan: the pruned scan wins
+// when m > q sqrt(P). (Measured at n = 1M, random queries: FP32 split scan faster at m = 8,192,
+// pruned faster at 32,768; FP64 about even at 8,192.)
+bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_idx,
+                    const Plan &pl)
 {
-    return precision == AIDW_F32C && ds.n_pad / kTileF32Knn <= kMaxCullTiles &&
-           m >= kCullMinQueries;
+    const double need = pl.knn.q_per_block * std::sqrt(static_cast<double>(pl.knn_slots));
+    return ds.n_pad / kTileF32Knn <= kMaxCullTiles && m >= kCullMinQueries &&
+           static_cast<double>(m) >= need && (precision == AIDW_F32C || !with_idx);
 }
 
-size_t culled_extra_bytes(int64_t m)
+size_t culled_extra_bytes(int64_t m, int precision)
 {
     const size_t mm = static_cast<size_t>(m);
-    return 4 * align256(mm * sizeof(uint32_t)) + align256(radix_scratch_bytes(m));
+    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    return 2 * align256(mm * sizeof(uint32_t)) + 2 * align256(mm * es) +
+           align256(radix_scratch_bytes(m));
 }
 
-// FP32 interpolation with Z-ordered queries and the pruned phase-1 scan: Morton keys of the
-// queries over the dataset's box, stable radix sort, gather, phase 1 (pruned), selection and
+// Interpolation with Z-ordered queries and the pruned phase-1 scan: Morton keys of the queries
+// over the dataset's box, stable radix sort, gather, phase 1 (pruned), selection and
 // finalisation writing back to the caller's order; phase 2 runs on the ordered queries.
 int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
-                   const aidw_params &p, const float *qx, const float *qy, const Scratch &sc,
-                   void *extra, float *out, float *out_alpha, int32_t *out_knn, cudaStream_t st,
+                   const aidw_params &p, const void *qx, const void *qy, const Scratch &sc,
+                   void *extra, void *out, float *out_alpha, int32_t *out_knn, cudaStream_t st,
                    bool profile)
 {
     const AlphaMap am = alpha_map(p);
     const int64_t m = pl.m;
+    const bool f64 = p.precision == AIDW_F64;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
     const size_t b4 = align256(static_cast<size_t>(m) * sizeof(uint32_t));
+    const size_t bq = align256(static_cast<size_t>(m) * es);
     char *e = static_cast<char *>(extra);
     uint32_t *keys = reinterpret_cast<uint32_t *>(e);
     uint32_t *perm = reinterpret_cast<uint32_t *>(e + b4);
-    float *sqx = reinterpret_cast<float *>(e + 2 * b4);
-    float *sqy = reinterpret_cast<float *>(e + 3 * b4);
-    void *sort_tmp = e + 4 * b4;
+    void *sqx = e + 2 * b4;
+    void *sqy = e + 2 * b4 + bq;
+    void *sort_tmp = e + 2 * b4 + 2 * bq;
     if (profile)
         cudaEventRecord(ctx->ev[0], st);
-    bool ok = morton_keys(qx, qy, nullptr, m, m, ds.box, keys, perm, st) == cudaSuccess;
-    ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
-    ok = ok && gather_queries(qx, qy, perm, m, sqx, sqy, st) == cudaSuccess;
-    ok = ok && launch_f32_knn_cull(ds, pl, sqx, sqy, p.k, sc, ctx->d_err, st) == cudaSuccess;
-    if (profile)
-        cudaEventRecord(ctx->ev[1], st);
-    ok = ok && launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
-                   cudaSuccess;
-    if (profile)
-        cudaEventRecord(ctx->ev[2], st);
-    ok = ok && launch_f32_weights(ds, pl, sqx, sqy, sc, ctx->d_err, st) == cudaSuccess;
-    if (profile)
-        cudaEventRecord(ctx->ev[3], st);
-    ok = ok && launch_f32_finalize(pl, sc, out, st, perm) == cudaSuccess;
+    bool ok;
+    if (f64) {
+        const double *x = static_cast<const double *>(qx), *y = static_cast<const double *>(qy);
+        double *sx = static_cast<double *>(sqx), *sy = static_cast<double *>(sqy);
+        ok = morton_keys_f64(x, y, m, ds.box, keys, perm, st) == cudaSuccess;
+        ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
+        ok = ok && gather_queries_f64(x, y, perm, m, sx, sy, st) == cudaSuccess;
+        ok = ok && launch_f64_knn_cull(ds, pl, sx, sy, p.k, sc, ctx->d_err, st) == cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[1], st);
+        ok = ok && launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
+                       cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[2], st);
+        ok = ok && launch_f64_weights(ds, pl, sx, sy, sc, ctx->d_err, st) == cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[3], st);
+        ok = ok && launch_f64_finalize(pl, sc, static_cast<double *>(out), st, perm) ==
+                       cudaSuccess;
+    } else {
+        const float *x = static_cast<const float *>(qx), *y = static_cast<const float *>(qy);
+        float *sx = static_cast<float *>(sqx), *sy = static_cast<float *>(sqy);
+        ok = morton_keys(x, y, nullptr, m, m, ds.box, keys, perm, st) == cudaSuccess;
+        ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
+        ok = ok && gather_queries(x, y, perm, m, sx, sy, st) == cudaSuccess;
+        ok = ok && launch_f32_knn_cull(ds, pl, sx, sy, p.k, sc, ctx->d_err, st) == cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[1], st);
+        ok = ok && launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
+                       cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[2], st);
+        ok = ok && launch_f32_weights(ds, pl, sx, sy, sc, ctx->d_err, st) == cudaSuccess;
+        if (profile)
+            cudaEventRecord(ctx->ev[3], st);
+        ok = ok && launch_f32_finalize(pl, sc, static_cast<float *>(out), st, perm) ==
+                       cudaSuccess;
+    }
     if (!ok)
         return AIDW_ERR_CUDA;
     if (profile) {
@@ -531,12 +571,14 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
 
     Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
                         force_knn_splits, force_w_splits, cfg);
-    const bool cull = force_knn_splits == 0 && use_culled_knn(p->precision, ds, m);
+    const bool cull =
+        force_knn_splits == 0 && use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl);
     if (cull) {
         pl.knn.splits = 1;
         pl.knn.split_len = ds.n_pad;
     }
-    const size_t sb = scratch_bytes(p->precision, pl, p->k) + (cull ? culled_extra_bytes(m) : 0);
+    const size_t sb = scratch_bytes(p->precision, pl, p->k) +
+                      (cull ? culled_extra_bytes(m, p->precision) : 0);
     // Staging for host arrays.
     const size_t b_q = (kq == 0 ? align256(m * es) : 0) + (kqy == 0 ? align256(m * es) : 0);
     const size_t b_o = ko == 0 ? align256(m * es) : 0;
@@ -582,9 +624,8 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         ctx_free(ctx, blk, total, st);
         return AIDW_ERR_CUDA;
     }
-    rc = cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, static_cast<const float *>(dqx),
-                               static_cast<const float *>(dqy), sc, extra,
-                               static_cast<float *>(dout), dalpha, dknn, st, ctx->profiling)
+    rc = cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, extra, dout, dalpha, dknn,
+                               st, ctx->profiling)
               : enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn,
                                       st, ctx->profiling);
     if (rc == AIDW_OK && host_any) {

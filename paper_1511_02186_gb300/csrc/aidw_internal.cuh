@@ -79,6 +79,7 @@ struct Plan {
     int kp;        // FP32 phase 1: register k-list length (8, 12, 16 or 32)
     int qw;        // FP32 phase 2: queries per thread (2, 4 or 8)
     int tw;        // FP32 phase 2: data points per shared-memory tile (256 or 512)
+    int knn_slots; // phase-1 CTAs resident on the whole GPU (occupancy x SMs)
 };
 
 // Per-query parameters of phase 2 produced by the selection kernel.
@@ -135,18 +136,28 @@ cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_
 cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st);
 cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
                            float *sqx, float *sqy, cudaStream_t st);
+cudaError_t morton_keys_f64(const double *x, const double *y, int64_t n, const float4 *box,
+                            uint32_t *keys, uint32_t *vals, cudaStream_t st);
+cudaError_t gather_queries_f64(const double *qx, const double *qy, const uint32_t *perm,
+                               int64_t m, double *sqx, double *sqy, cudaStream_t st);
 
 cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *qx,
                            const double *qy, int k, const Scratch &sc, int *err,
                            cudaStream_t st);
 cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
-                              cudaStream_t st);
+                              cudaStream_t st, const uint32_t *perm = nullptr);
+// Phase 1 over Z-ordered FP64 queries, pruned like launch_f32_knn_cull, distances only (the
+// neighbour distances, not which of tied points, decide r_obs); sqx / sqy are the queries in
+// Z-order and the dataset's points are read through its Z-order map.
+cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const double *sqx,
+                                const double *sqy, int k, const Scratch &sc, int *err,
+                                cudaStream_t st);
 cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
                                const double *qy, const Scratch &sc, int *err,
                                cudaStream_t st);
 cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
-                                cudaStream_t st);
+                                cudaStream_t st, const uint32_t *perm = nullptr);
 
 // Shape of the kernels: queries per CTA of each scan and the CTA slots per SM that occupancy
 // allows (used to cut splits into whole waves). FP32 shapes follow the tuning fields of

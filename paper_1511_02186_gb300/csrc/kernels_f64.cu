@@ -182,11 +182,200 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Phase 1 over Z-ordered FP64 queries, pruned as the FP32 path's (one CTA per query block, data
+// tiles visited in order of a lower bound of the box-to-box distance, nearest centre first among
+// equal bounds, the block stopping at the first tile beyond its queries' largest k-th distance,
+// each warp skipping tiles beyond its own), keeping distances only: the k nearest distances, and
+// so r_obs, do not depend on which of two tied points is kept. A tile's points are gathered from
+// the caller-order FP64 copy through the Z-order map. The tile boxes hold the FP32 coordinates;
+// widened by 2^-23 of their largest magnitude they contain the FP64 points (FP32 rounding moves a
+// coordinate by at most 2^-24 of it), and the bound is shrunk by 2^-50 to cover its own rounding
+// and that of the exact distance, so no skipped point could have entered a list.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double box_bound64(float4 tb, double qx0, double qy0, double qx1,
+                                              double qy1)
+{
+    const double bx0 = tb.x, by0 = tb.y, bx1 = tb.z, by1 = tb.w;
+    const double mag = fmax(fmax(fabs(bx0), fabs(bx1)), fmax(fabs(by0), fabs(by1)));
+    const double d = mag * 0x1p-23 + 0x1p-140;
+    const double dx = fmax(0.0, fmax((bx0 - d) - qx1, qx0 - (bx1 + d)));
+    const double dy = fmax(0.0, fmax((by0 - d) - qy1, qy0 - (by1 + d)));
+    return (dx * dx + dy * dy) * (1.0 - 0x1p-50);
+}
+
+template <int KP, int Q>
+__global__ void __launch_bounds__(kThreads)
+f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2,
+                    const double *__restrict__ sqx, const double *__restrict__ sqy, int k,
+                    double *__restrict__ part_d2)
+{
+    extern __shared__ unsigned long long order[];  // [ntiles_p2] sort keys
+    __shared__ __align__(16) double2 tile[kTileF32Knn];
+    constexpr int W = kThreads / 32;
+    __shared__ double red[4][W];
+    __shared__ double sbox[4];
+    __shared__ double sthr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t qbase = static_cast<int64_t>(blockIdx.x) * qpb;
+    const int64_t wbase = qbase + static_cast<int64_t>(warp) * 32 * Q + lane;
+
+    double qxr[Q], qyr[Q];
+    double L[Q][KP];
+    double bx0 = CUDART_INF, by0 = CUDART_INF, bx1 = -CUDART_INF, by1 = -CUDART_INF;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = min(wbase + j * 32, m - 1);
+        qxr[j] = sqx[q];
+        qyr[j] = sqy[q];
+        bx0 = fmin(bx0, qxr[j]);
+        by0 = fmin(by0, qyr[j]);
+        bx1 = fmax(bx1, qxr[j]);
+        by1 = fmax(by1, qyr[j]);
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+            L[j][i] = (i < KP - k) ? -CUDART_INF : CUDART_INF;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bx0 = fmin(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+        by0 = fmin(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+        bx1 = fmax(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+        by1 = fmax(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+    }
+    const double wx0 = bx0, wy0 = by0, wx1 = bx1, wy1 = by1;  // the warp's query box
+    double wthr = CUDART_INF;
+    if (lane == 0) {
+        red[0][warp] = bx0;
+        red[1][warp] = by0;
+        red[2][warp] = bx1;
+        red[3][warp] = by1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double b0 = red[0][0], b1 = red[1][0], b2 = red[2][0], b3 = red[3][0];
+        for (int w = 1; w < W; ++w) {
+            b0 = fmin(b0, red[0][w]);
+            b1 = fmin(b1, red[1][w]);
+            b2 = fmax(b2, red[2][w]);
+            b3 = fmax(b3, red[3][w]);
+        }
+        sbox[0] = b0;
+        sbox[1] = b1;
+        sbox[2] = b2;
+        sbox[3] = b3;
+        sthr = CUDART_INF;
+    }
+    __syncthreads();
+    const double qx0 = sbox[0], qy0 = sbox[1], qx1 = sbox[2], qy1 = sbox[3];
+    const float qcx = static_cast<float>(0.5 * (qx0 + qx1));
+    const float qcy = static_cast<float>(0.5 * (qy0 + qy1));
+    // Keys: bound rounded down to FP32 (32 bits), centre distance (19 bits), tile (13 bits).
+    for (int t = tid; t < ntiles_p2; t += kThreads) {
+        unsigned long long key = ~0ull;
+        if (t < ntiles) {
+            const float4 tb = ds.tile_box[t];
+            const float lb = __double2float_rd(box_bound64(tb, qx0, qy0, qx1, qy1));
+            const float cx = 0.5f * (tb.x + tb.z) - qcx, cy = 0.5f * (tb.y + tb.w) - qcy;
+            const float cd = fminf(fmaf(cx, cx, cy * cy), 3.0e38f);
+            key = (static_cast<unsigned long long>(__float_as_uint(fmaxf(lb, 0.0f))) << 32) |
+                  (static_cast<unsigned long long>(__float_as_uint(cd) >> 13) << 13) |
+                  static_cast<unsigned long long>(t);
+        }
+        order[t] = key;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= ntiles_p2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < ntiles_p2; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = order[i], b = order[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((a > b) == up) {
+                        order[i] = b;
+                        order[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    for (int i = 0; i < ntiles; ++i) {
+        const unsigned long long key = order[i];
+        if (static_cast<double>(__uint_as_float(static_cast<uint32_t>(key >> 32))) > sthr)
+            break;
+        const int64_t t = static_cast<int64_t>(key & 0x1fffull);
+        for (int u = tid; u < kTileF32Knn; u += kThreads) {
+            const int32_t o = ds.orig[t * kTileF32Knn + u];
+            tile[u] = o >= 0 ? ds.xy64[o] : make_double2(CUDART_INF, CUDART_INF);
+        }
+        __syncthreads();
+        const double wlb = box_bound64(ds.tile_box[t], wx0, wy0, wx1, wy1);
+        if (!(wlb > wthr)) {
+            for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
+                double mn[Q];
+#pragma unroll
+                for (int j = 0; j < Q; ++j)
+                    mn[j] = CUDART_INF;
+#pragma unroll
+                for (int u = 0; u < kChunkKnn; ++u) {
+                    const double2 p = tile[c + u];
+#pragma unroll
+                    for (int j = 0; j < Q; ++j)
+                        mn[j] = fmin(mn[j], dist2_exact(qxr[j], qyr[j], p.x, p.y));
+                }
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    if (mn[j] < L[j][KP - 1]) {
+#pragma unroll 1
+                        for (int u = 0; u < kChunkKnn; ++u) {
+                            const double2 p = tile[c + u];
+                            const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
+                            if (d < L[j][KP - 1])
+                                list_insert<KP>(L[j], d);
+                        }
+                    }
+                }
+            }
+        }
+        double mx = -CUDART_INF;
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            mx = fmax(mx, L[j][KP - 1]);
+        for (int o = 16; o > 0; o >>= 1)
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        wthr = mx;
+        if (lane == 0)
+            red[0][warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            double v = red[0][0];
+            for (int w = 1; w < W; ++w)
+                v = fmax(v, red[0][w]);
+            sthr = v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t q = wbase + j * 32;
+        if (q >= m)
+            continue;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            const int r = i - (KP - k);
+            if (r >= 0)
+                part_d2[static_cast<int64_t>(r) * m + q] = L[j][i];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
                   const double *__restrict__ part_d2, const int32_t *__restrict__ part_idx,
                   QParamF64 *__restrict__ qp, float *__restrict__ out_alpha,
-                  int32_t *__restrict__ out_knn)
+                  int32_t *__restrict__ out_knn, const uint32_t *__restrict__ perm)
 {
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= m)
@@ -235,7 +424,7 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     }
     qp[q] = o;
     if (out_alpha)
-        out_alpha[q] = static_cast<float>(alpha);
+        out_alpha[perm ? perm[q] : q] = static_cast<float>(alpha);
 }
 
 template <int Q>
@@ -346,7 +535,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
 
 __global__ void __launch_bounds__(256)
 f64_finalize_kernel(int64_t m, int S, const double *__restrict__ part_sum,
-                    double *__restrict__ out)
+                    double *__restrict__ out, const uint32_t *__restrict__ perm)
 {
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= m)
@@ -359,7 +548,7 @@ f64_finalize_kernel(int64_t m, int S, const double *__restrict__ part_sum,
         kahan_add(WZ, WZc, o[2 * m]);
         kahan_add(WZ, WZc, o[3 * m]);
     }
-    out[q] = (WZ - WZc) / (W - Wc);  // Eq. 1
+    out[perm ? perm[q] : q] = (WZ - WZc) / (W - Wc);  // Eq. 1
 }
 
 template <int KP>
@@ -449,14 +638,46 @@ cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *q
 
 cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
-                              cudaStream_t st)
+                              cudaStream_t st, const uint32_t *perm)
 {
     const int64_t blocks = (pl.m + 255) / 256;
     f64_select_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         pl.m, pl.knn.splits, k, r_exp, am, static_cast<const double *>(sc.part_d2),
         pl.with_idx ? sc.part_idx : nullptr, static_cast<QParamF64 *>(sc.qparam), out_alpha,
-        out_knn);
+        out_knn, perm);
     return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t launch_cull64_t(const DatasetDev &ds, const Plan &pl, const double *sqx,
+                            const double *sqy, int k, const Scratch &sc, cudaStream_t st)
+{
+    constexpr int Q = knn_q64<KP>();
+    const int ntiles = static_cast<int>(ds.n_pad / kTileF32Knn);
+    int p2 = 1;
+    while (p2 < ntiles)
+        p2 <<= 1;
+    const size_t dyn = sizeof(unsigned long long) * p2;
+    auto fn = f64_knn_cull_kernel<KP, Q>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(dyn));
+    if (e != cudaSuccess)
+        return e;
+    fn<<<pl.knn.qblocks, kThreads, dyn, st>>>(ds, pl.m, pl.knn.q_per_block, ntiles, p2, sqx,
+                                              sqy, k, static_cast<double *>(sc.part_d2));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const double *sqx,
+                                const double *sqy, int k, const Scratch &sc, int *err,
+                                cudaStream_t st)
+{
+    (void)err;  // no bounded waits: tiles are gathered with plain loads
+    if (k <= 8)
+        return launch_cull64_t<8>(ds, pl, sqx, sqy, k, sc, st);
+    if (k <= 16)
+        return launch_cull64_t<16>(ds, pl, sqx, sqy, k, sc, st);
+    return launch_cull64_t<32>(ds, pl, sqx, sqy, k, sc, st);
 }
 
 cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
@@ -470,11 +691,11 @@ cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const doubl
 }
 
 cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
-                                cudaStream_t st)
+                                cudaStream_t st, const uint32_t *perm)
 {
     const int64_t blocks = (pl.m + 255) / 256;
     f64_finalize_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
-        pl.m, pl.w.splits, static_cast<const double *>(sc.part_sum), out);
+        pl.m, pl.w.splits, static_cast<const double *>(sc.part_sum), out, perm);
     return cudaGetLastError();
 }
 

@@ -203,9 +203,23 @@ __global__ void tile_box_kernel(const float4 *__restrict__ nxy2, int64_t ntiles,
         boxes[t] = make_float4(x0, y0, x1, y1);
 }
 
-__global__ void gather_pairs_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                    const uint32_t *__restrict__ perm, int64_t m, float *sx,
-                                    float *sy)
+// Morton keys of FP64 query coordinates (rounded to FP32 for the key: the key only orders).
+__global__ void morton_keys_f64_kernel(const double *__restrict__ x,
+                                       const double *__restrict__ y, int64_t n,
+                                       const float4 *__restrict__ box, uint32_t *keys,
+                                       uint32_t *vals)
+{
+    const float4 b = *box;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        keys[i] = morton_of(static_cast<float>(x[i]), static_cast<float>(y[i]), b);
+        vals[i] = static_cast<uint32_t>(i);
+    }
+}
+
+template <typename T>
+__global__ void gather_pairs_kernel(const T *__restrict__ x, const T *__restrict__ y,
+                                    const uint32_t *__restrict__ perm, int64_t m, T *sx, T *sy)
 {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -290,7 +304,23 @@ cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaSt
 cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
                            float *sqx, float *sqy, cudaStream_t st)
 {
-    gather_pairs_kernel<<<grid_for(m, 256, 4096), 256, 0, st>>>(qx, qy, perm, m, sqx, sqy);
+    gather_pairs_kernel<float><<<grid_for(m, 256, 4096), 256, 0, st>>>(qx, qy, perm, m, sqx,
+                                                                       sqy);
+    return cudaGetLastError();
+}
+
+cudaError_t morton_keys_f64(const double *x, const double *y, int64_t n, const float4 *box,
+                            uint32_t *keys, uint32_t *vals, cudaStream_t st)
+{
+    morton_keys_f64_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(x, y, n, box, keys, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_queries_f64(const double *qx, const double *qy, const uint32_t *perm,
+                               int64_t m, double *sqx, double *sqy, cudaStream_t st)
+{
+    gather_pairs_kernel<double><<<grid_for(m, 256, 4096), 256, 0, st>>>(qx, qy, perm, m, sqx,
+                                                                        sqy);
     return cudaGetLastError();
 }
 

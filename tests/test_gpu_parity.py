@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from paper_1511_02186_gb300 import aidw, workloads
-from parity import TOL_F32, assert_parity, oracle_for, params_of, rel_err, run_gpu, to_device
+from parity import (TOL_F32, TOL_F64, assert_parity, oracle_for, params_of, rel_err, run_gpu,
+                    to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -234,4 +235,80 @@ def test_budget_and_injected_allocation_failure(ctx):
     assert e.value.status == aidw.ERR_OOM
     out, _, _ = ctx.interpolate(ds, qx, qy, aidw.default_params())  # recovers
     assert np.all(np.isfinite(out.cpu().numpy()))
+    ds.destroy()
+
+
+def _fp64_cases():
+    rng = np.random.default_rng(91)
+    # Enough queries (m > block size x sqrt(resident blocks)) for the pruned phase 1.
+    cases = [workloads.small_case(92, 30011, 12003, k=10, pattern="uniform", side=800.0),
+             workloads.small_case(93, 50000, 12288, k=17, pattern="clustered", side=300.0),
+             workloads.small_case(94, 20000, 9000, k=32, pattern="clustered", side=50.0)]
+    # Integer lattice (exact ties everywhere), queries on half-integers and on points.
+    g = np.arange(60, dtype=float)
+    gx, gy = np.meshgrid(g, g)
+    perm = rng.permutation(3600)
+    qx = rng.integers(0, 120, 12000) / 2.0
+    qy = rng.integers(0, 120, 12000) / 2.0
+    cases.append(workloads.Workload("lattice64", gx.ravel()[perm], gy.ravel()[perm],
+                                    rng.standard_normal(3600), 3600.0, qx, qy, k=9))
+    # Large coordinates with small spacing: FP32 rounding moves points by up to 1/16, far more
+    # than their spacing, so the FP32 tile boxes alone would not bound the FP64 distances.
+    x = 1.0e6 + rng.uniform(0, 40, 30000)
+    y = -2.0e6 + rng.uniform(0, 40, 30000)
+    cases.append(workloads.Workload("offset", x, y, rng.standard_normal(30000), 1600.0,
+                                    1.0e6 + rng.uniform(0, 40, 12000),
+                                    -2.0e6 + rng.uniform(0, 40, 12000), k=10))
+    return cases
+
+
+@pytest.mark.parametrize("idx", range(5), ids=["uniform", "clustered_k17", "clustered_k32",
+                                               "lattice_ties", "large_offset"])
+def test_fp64_pruned_knn_equals_caller_order_scan(ctx, idx):
+    """FP64 calls without the kNN output take the pruned phase 1 over Z-ordered queries; with it,
+    the caller-order scan. Both give the same neighbour distances, hence bit-identical alpha and
+    Z, and both match the oracle at 1e-12."""
+    import torch
+    wl = _fp64_cases()[idx]
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F64)
+    p = aidw.default_params(k=wl.k, precision=aidw.F64)
+    ctx.set_profiling(True)
+    z1, a1, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True)
+    assert ctx.kernel_times().launches == 18  # ordering + pruned phase 1
+    z2, a2, kn = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    assert ctx.kernel_times().launches == 4   # caller-order scan
+    ctx.set_profiling(False)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2)
+    assert torch.equal(z1, z2)
+    ref, src = oracle_for(wl, aidw.F64)
+    assert rel_err(z1.cpu().numpy(), ref).max() <= TOL_F64
+    assert np.array_equal(kn.cpu().numpy(), ref["knn"])
+    ds.destroy()
+
+
+@pytest.mark.parametrize("pattern", ["uniform", "clustered"])
+def test_fp32_pruned_knn_equals_split_scan(ctx, pattern):
+    """FP32 with enough queries for the pruned phase 1 against the forced split scan: kNN sets
+    equal up to FP32 distance ties, alpha within FP32 rounding, both Z within tolerance of the
+    oracle."""
+    import torch
+    wl = workloads.small_case(95, 60000, 20000, k=10, pattern=pattern, side=500.0)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F32C)
+    p = params_of(wl, aidw.F32C)
+    ctx.set_profiling(True)
+    z1, a1, k1 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    assert ctx.kernel_times().launches == 18  # ordering + pruned phase 1
+    z2, a2, k2 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True, splits=(8, 0))
+    assert ctx.kernel_times().launches == 4
+    ctx.set_profiling(False)
+    torch.cuda.synchronize()
+    ref, src = oracle_for(wl, aidw.F32C)
+    for z in (z1, z2):
+        assert rel_err(z.cpu().numpy(), ref).max() <= TOL_F32
+    same = np.mean([set(a) == set(b) for a, b in zip(k1.cpu().numpy(), k2.cpu().numpy())])
+    assert same >= 0.999
+    assert np.abs(a1.cpu().numpy() - a2.cpu().numpy()).max() <= 1e-5
     ds.destroy()
