@@ -312,3 +312,74 @@ def test_fp32_pruned_knn_equals_split_scan(ctx, pattern):
     assert same >= 0.999
     assert np.abs(a1.cpu().numpy() - a2.cpu().numpy()).max() <= 1e-5
     ds.destroy()
+
+
+def _degenerate_cases():
+    rng = np.random.default_rng(97)
+    out = []
+    # Every data point at one location (zero-area bounding box), queries around and on it.
+    x = np.full(3000, 12.5)
+    y = np.full(3000, -3.0)
+    qx = np.concatenate([[12.5], rng.uniform(0, 25, 2999)])
+    qy = np.concatenate([[-3.0], rng.uniform(-15, 9, 2999)])
+    out.append(workloads.Workload("one_location", x, y, rng.standard_normal(3000), 600.0,
+                                  qx, qy, k=10))
+    # k = n (every point is a neighbour).
+    x, y = rng.uniform(0, 1, 12), rng.uniform(0, 1, 12)
+    out.append(workloads.Workload("k_equals_n", x, y, rng.standard_normal(12), 1.0,
+                                  rng.uniform(0, 1, 300), rng.uniform(0, 1, 300), k=12))
+    # Collinear data (zero width in y), queries off the line.
+    x = rng.uniform(0, 100, 5000)
+    out.append(workloads.Workload("collinear", x, np.zeros(5000), np.sin(x), 100.0,
+                                  rng.uniform(0, 100, 2500), rng.uniform(-5, 5, 2500), k=8))
+    # Two dense clusters 1e4 apart: weights span hundreds of decades.
+    x = np.concatenate([rng.normal(0, 0.01, 2000), rng.normal(1e4, 0.01, 2000)])
+    y = np.concatenate([rng.normal(0, 0.01, 2000), rng.normal(0, 0.01, 2000)])
+    z = np.concatenate([np.ones(2000), -np.ones(2000)]) + 0.01 * rng.standard_normal(4000)
+    out.append(workloads.Workload("two_clusters", x, y, z, 1e8,
+                                  rng.uniform(-1, 1e4 + 1, 2500), rng.uniform(-1, 1, 2500),
+                                  k=10))
+    # Large coordinate offset with small spacing (FP32 coordinates near 1e5).
+    x = 1.0e5 + rng.uniform(0, 50, 8000)
+    y = 2.0e5 + rng.uniform(0, 50, 8000)
+    out.append(workloads.Workload("offset_1e5", x, y, np.cos(x / 7), 2500.0,
+                                  1.0e5 + rng.uniform(0, 50, 3000),
+                                  2.0e5 + rng.uniform(0, 50, 3000), k=10))
+    return out
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("idx", range(5), ids=["one_location", "k_equals_n", "collinear",
+                                               "two_clusters", "offset_1e5"])
+def test_degenerate_inputs(ctx, precision, idx):
+    """Zero-area and zero-width data, k = n, weights spanning hundreds of decades, and large
+    coordinate offsets: the same parity as the regular cases."""
+    wl = _degenerate_cases()[idx]
+    assert_parity(ctx, wl, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_empty_query_set_and_empty_dataset(ctx, precision):
+    """m = 0 is a no-op for every entry point (outputs untouched); n = 0 is rejected."""
+    import torch
+    wl = workloads.small_case(121, 50, 5, k=3)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    dt = torch.float64 if precision == aidw.F64 else torch.float32
+    e = torch.empty(0, dtype=dt, device="cuda")
+    p = aidw.default_params(k=3, precision=precision)
+    out, a, kn = ctx.interpolate(ds, e, e, p, want_alpha=True, want_knn=True)
+    torch.cuda.synchronize()
+    assert out.numel() == 0 and a.numel() == 0 and kn.numel() == 0
+    out = ctx.idw(ds, e, e, 2.0, precision=precision)
+    assert out.numel() == 0
+    h = np.zeros(0, dtype=np.float64 if precision == aidw.F64 else np.float32)
+    out, _, _ = ctx.interpolate(ds, h, h, p)
+    assert out.shape == (0,)
+    if precision == aidw.F64:
+        rc, rid = ctx.submit(ds, h, h, p, np.zeros(0))
+        assert rc == aidw.OK and ctx.wait(rid, 10_000_000) == aidw.OK
+        ctx.release(rid)
+    ds.destroy()
+    with pytest.raises(aidw.AidwError) as err:
+        ctx.create_dataset(np.zeros(0), np.zeros(0), np.zeros(0), 1.0)
+    assert err.value.status == aidw.ERR_INVALID_ARG
