@@ -640,7 +640,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded uniform points, BASELINE config 2 shape)",
+            "data": "synthetic (seeded uniform points in [0,1000]^2, n = m = 1,048,576)",
             "config": workload_config(wl),
             "queries_per_s": world * wl.m * args.steps / total_s,
             "kernel_ms": {"knn_incl_query_ordering": kn, "select": ks, "weights": kw,

@@ -250,7 +250,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
 }
 
 // Thread 0 waits (bounded: max_polls acquire loads, 256 ns apart at least) until
-// *p >= target; the verdict is shared with the CTA through the shared word `flag`.
+// *p >= target; the outcome is shared with the CTA through the shared word `flag`.
 __device__ __forceinline__ bool cta_wait_count(const uint32_t *p, uint32_t target, int *flag,
                                                uint32_t max_polls = kMaxWaitPolls)
 {
