@@ -212,11 +212,14 @@ typedef struct aidw_tune_config {
     int32_t split_points;       /* batches: data points per phase-2 work unit, a multiple of
                                  * 2,048 in [2,048, 4,194,304] */
     int32_t ctas_per_sm;        /* batches: persistent CTAs per SM, 0 = as many as fit */
-    int32_t reserved[3];        /* zero */
+    int32_t knn_queries_per_thread; /* pruned phase 1: 2 or 4 queries per thread (query block
+                                 * 128x), 0 = 4 for lists of up to 16, else 2; lists of 32
+                                 * always take 2 */
+    int32_t reserved[2];        /* zero */
 } aidw_tune_config;
 
 /* Fills the built-in shape: 4 queries per thread, 512-point tiles, the smallest list, 65,536
- * points per batch work unit, full occupancy. */
+ * points per batch work unit, full occupancy, phase-1 queries per thread by list length. */
 int aidw_tune_config_default(aidw_tune_config *out);
 /* AIDW_OK if every field is one of the values above, else AIDW_ERR_INVALID_ARG. */
 int aidw_tune_config_check(const aidw_tune_config *cfg);
@@ -236,8 +239,8 @@ int aidw_get_tune_config(aidw_ctx *ctx, aidw_tune_config *out);
 
 /* Times an FP32 interpolation (arguments as aidw_interpolate, device arrays only) under
  * candidate shapes by coordinate search from the context's shape (queries per thread, tile
- * points, k-list length; each candidate run `reps` times after one warm-up, fastest run
- * counts) and returns the fastest in *best with its time in *best_ms. `out` receives the
+ * points, k-list length, phase-1 queries per thread; each candidate run `reps` times after one
+ * warm-up, fastest run counts) and returns the fastest in *best with its time in *best_ms. `out` receives the
  * results of the last run. Synchronous. Errors: as aidw_interpolate; INVALID_ARG for host
  * arrays, F64 or reps < 1. */
 int aidw_autotune_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy,
@@ -249,7 +252,8 @@ int aidw_batch_set_config(aidw_ctx *ctx, aidw_batch *batch, const aidw_tune_conf
 int aidw_batch_get_config(aidw_ctx *ctx, aidw_batch *batch, aidw_tune_config *out);
 
 /* Times the prepared batch under candidate shapes by coordinate search from its current one
- * (queries per thread, tile points, k-list length, points per work unit, CTAs per SM; each
+ * (queries per thread, tile points, k-list length, phase-1 queries per thread, points per work
+ * unit, CTAs per SM; each
  * candidate launched `reps` times after one warm-up, fastest launch counts), leaves the batch
  * prepared with the fastest and returns it. Synchronous; after a search the batch's outputs
  * hold the winner's results. Errors: INVALID_ARG, NOT_FOUND (a dataset was destroyed), OOM,
@@ -261,7 +265,7 @@ int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *batch, int32_t reps, uint32_t
  * characters; the autotuner's keys name the device and the workload's size class) mapped to
  * shapes. Files hold one JSON object per line:
  *   {"key": "...", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
- *    "split_points": 65536, "ctas_per_sm": 0, "ms": 91.5}
+ *    "split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "ms": 91.5}
  * _load merges a file into the cache (INVALID_ARG on a malformed line, NOT_FOUND if the file
  * cannot be opened; nothing is merged on error); _save writes the whole cache; _get returns
  * NOT_FOUND for an unknown key. Host only: usable without a GPU. */

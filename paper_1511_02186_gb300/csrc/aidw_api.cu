@@ -257,6 +257,7 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     pl.m = m;
     pl.with_idx = with_idx;
     pl.kp = f32_list_length(k, tc.knn_list);
+    pl.kq = f64 ? (k <= 16 ? 2 : 1) : cull_queries_per_thread(pl.kp, tc.knn_queries_per_thread);
     pl.qw = tc.queries_per_thread;
     pl.tw = tc.tile_points;
     int &ks = ctx->slots_cache[precision][kp_bucket(f64 ? k : pl.kp)][with_idx ? 1 : 0];
@@ -423,7 +424,7 @@ constexpr int64_t kCullMinQueries = 2048;
 bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_idx,
                     const Plan &pl)
 {
-    const double need = pl.knn.q_per_block * std::sqrt(static_cast<double>(pl.knn_slots));
+    const double need = kThreads * pl.kq * std::sqrt(static_cast<double>(pl.knn_slots));
     return ds.n_pad / kTileF32Knn <= kMaxCullTiles && m >= kCullMinQueries &&
            static_cast<double>(m) >= need && (precision == AIDW_F32C || !with_idx);
 }
@@ -576,6 +577,8 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
     if (cull) {
         pl.knn.splits = 1;
         pl.knn.split_len = ds.n_pad;
+        pl.knn.q_per_block = kThreads * pl.kq;
+        pl.knn.qblocks = static_cast<int>((m + pl.knn.q_per_block - 1) / pl.knn.q_per_block);
     }
     const size_t sb = scratch_bytes(p->precision, pl, p->k) +
                       (cull ? culled_extra_bytes(m, p->precision) : 0);

@@ -80,6 +80,7 @@ struct Plan {
     int qw;        // FP32 phase 2: queries per thread (2, 4 or 8)
     int tw;        // FP32 phase 2: data points per shared-memory tile (256 or 512)
     int knn_slots; // phase-1 CTAs resident on the whole GPU (occupancy x SMs)
+    int kq;        // pruned phase 1: queries per thread (2 or 4)
 };
 
 // Per-query parameters of phase 2 produced by the selection kernel.
@@ -168,6 +169,12 @@ int f32_knn_slots_per_sm(int kp, bool with_idx);
 int f32_w_slots_per_sm(int qw, int tw);
 // k-list length for k under a minimum (aidw_tune_config.knn_list).
 int f32_list_length(int k, int kp_min);
+// Queries per thread of the pruned phase 1 for list length kp under the shape's request
+// (aidw_tune_config.knn_queries_per_thread; 0 = 4 for lists of up to 16, lists of 32 take 2).
+inline int cull_queries_per_thread(int kp, int requested)
+{
+    return kp > 16 ? 2 : (requested == 2 ? 2 : 4);
+}
 // Built-in shape and the check of a caller's shape (autotune.cu).
 aidw_tune_config tune_default();
 bool tune_valid(const aidw_tune_config &c);

@@ -28,6 +28,7 @@ aidw_tune_config tune_default()
     c.knn_list = 0;
     c.split_points = 65536;
     c.ctas_per_sm = 0;
+    c.knn_queries_per_thread = 0;
     return c;
 }
 
@@ -40,8 +41,9 @@ bool tune_valid(const aidw_tune_config &c)
     const bool sp = c.split_points >= kPadPoints && c.split_points <= (1 << 22) &&
                     c.split_points % kPadPoints == 0;
     const bool ct = c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
-    return qw && tw && kl && sp && ct && c.reserved[0] == 0 && c.reserved[1] == 0 &&
-           c.reserved[2] == 0;
+    const bool kq = c.knn_queries_per_thread == 0 || c.knn_queries_per_thread == 2 ||
+                    c.knn_queries_per_thread == 4;
+    return qw && tw && kl && sp && ct && kq && c.reserved[0] == 0 && c.reserved[1] == 0;
 }
 
 namespace {
@@ -50,7 +52,8 @@ bool same(const aidw_tune_config &a, const aidw_tune_config &b)
 {
     return a.queries_per_thread == b.queries_per_thread && a.tile_points == b.tile_points &&
            a.knn_list == b.knn_list && a.split_points == b.split_points &&
-           a.ctas_per_sm == b.ctas_per_sm;
+           a.ctas_per_sm == b.ctas_per_sm &&
+           a.knn_queries_per_thread == b.knn_queries_per_thread;
 }
 
 // ---- process-wide cache -----------------------------------------------------------------------
@@ -88,10 +91,11 @@ bool parse_line(const char *line, std::string *key, CacheEntry *e)
     const int got = std::sscanf(
         line,
         " { \"key\" : \"%255[^\"]\" , \"queries_per_thread\" : %d , \"tile_points\" : %d , "
-        "\"knn_list\" : %d , \"split_points\" : %d , \"ctas_per_sm\" : %d , \"ms\" : %lf } %n",
+        "\"knn_list\" : %d , \"split_points\" : %d , \"ctas_per_sm\" : %d , "
+        "\"knn_queries_per_thread\" : %d , \"ms\" : %lf } %n",
         kbuf, &c.queries_per_thread, &c.tile_points, &c.knn_list, &c.split_points,
-        &c.ctas_per_sm, &ms, &used);
-    if (got != 7 || used < 0 || line[used] != '\0')
+        &c.ctas_per_sm, &c.knn_queries_per_thread, &ms, &used);
+    if (got != 8 || used < 0 || line[used] != '\0')
         return false;
     if (!key_valid(kbuf) || !tune_valid(c) || !std::isfinite(ms))
         return false;
@@ -274,9 +278,10 @@ int aidw_tune_cache_save(const char *path)
             ok &= std::fprintf(f,
                                "{\"key\": \"%s\", \"queries_per_thread\": %d, \"tile_points\": "
                                "%d, \"knn_list\": %d, \"split_points\": %d, \"ctas_per_sm\": %d, "
-                               "\"ms\": %.6f}\n",
+                               "\"knn_queries_per_thread\": %d, \"ms\": %.6f}\n",
                                kv.first.c_str(), c.queries_per_thread, c.tile_points,
-                               c.knn_list, c.split_points, c.ctas_per_sm, kv.second.ms) > 0;
+                               c.knn_list, c.split_points, c.ctas_per_sm,
+                               c.knn_queries_per_thread, kv.second.ms) > 0;
         }
     }
     ok &= std::fclose(f) == 0;
@@ -380,14 +385,20 @@ int aidw_autotune_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, co
         };
         const int k = p->k;
         auto skip = [&](const aidw_tune_config &c, const aidw_tune_config &b) {
-            // Same k-list length: nothing to time.
-            return c.knn_list != b.knn_list &&
-                   f32_list_length(k, c.knn_list) == f32_list_length(k, b.knn_list);
+            // The same kernels as the shape already timed: nothing to time.
+            const int kc = f32_list_length(k, c.knn_list), kb = f32_list_length(k, b.knn_list);
+            return kc == kb &&
+                   cull_queries_per_thread(kc, c.knn_queries_per_thread) ==
+                       cull_queries_per_thread(kb, b.knn_queries_per_thread) &&
+                   c.queries_per_thread == b.queries_per_thread &&
+                   c.tile_points == b.tile_points && c.split_points == b.split_points &&
+                   c.ctas_per_sm == b.ctas_per_sm;
         };
         const std::vector<Field> fields = {
             {&aidw_tune_config::queries_per_thread, {2, 4, 8}},
             {&aidw_tune_config::tile_points, {256, 512}},
             {&aidw_tune_config::knn_list, {0, 16, 32}},
+            {&aidw_tune_config::knn_queries_per_thread, {0, 2, 4}},
         };
         rc = coordinate_search(fields, &cfg, &ms, measure, skip);
         if (rc == AIDW_OK && (flags & AIDW_TUNE_CACHE))
@@ -472,18 +483,25 @@ int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *b, int32_t reps, uint32_t fla
             return r;
         };
         auto skip = [&](const aidw_tune_config &c, const aidw_tune_config &bb) {
-            if (c.knn_list == bb.knn_list)
+            // The same kernels for every item as the shape already timed: nothing to time.
+            if (c.queries_per_thread != bb.queries_per_thread ||
+                c.tile_points != bb.tile_points || c.split_points != bb.split_points ||
+                c.ctas_per_sm != bb.ctas_per_sm)
                 return false;
-            for (const aidw_batch_item &it : b->items)
-                if (f32_list_length(it.params.k, c.knn_list) !=
-                    f32_list_length(it.params.k, bb.knn_list))
+            for (const aidw_batch_item &it : b->items) {
+                const int kc = f32_list_length(it.params.k, c.knn_list);
+                const int kb = f32_list_length(it.params.k, bb.knn_list);
+                if (kc != kb || cull_queries_per_thread(kc, c.knn_queries_per_thread) !=
+                                    cull_queries_per_thread(kb, bb.knn_queries_per_thread))
                     return false;
+            }
             return true;
         };
         const std::vector<Field> fields = {
             {&aidw_tune_config::queries_per_thread, {2, 4, 8}},
             {&aidw_tune_config::tile_points, {256, 512}},
             {&aidw_tune_config::knn_list, {0, 16, 32}},
+            {&aidw_tune_config::knn_queries_per_thread, {0, 2, 4}},
             {&aidw_tune_config::split_points, {16384, 32768, 65536, 131072, 262144}},
             {&aidw_tune_config::ctas_per_sm, ctas},
         };

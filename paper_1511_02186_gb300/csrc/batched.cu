@@ -46,7 +46,7 @@ struct BatchItemDev {
     const float *qx, *qy;
     float *out, *out_alpha;
     int64_t m;
-    int32_t k, kp;
+    int32_t k, kp, kq;  // kq: queries per thread of the pruned phase-1 units
     double r_exp;
     AlphaMap am;
     PassPlan knn, w;
@@ -136,28 +136,35 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 cta_publish(&it.cnt_knn[wu.qblock]);
         } else if (wu.type == kUnitKnn) {
             const int64_t qbase = static_cast<int64_t>(wu.qblock) * it.knn.q_per_block;
+#define AIDW_CULL_UNIT(KP, Q)                                                                  \
+    ok = knn_cull_unit<KP, Q, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2, it.sqx, it.sqy, \
+                                     it.k, it.part_d2, nullptr, err, ktile, ts, order, nullptr,  \
+                                     cs)
+            const bool q2 = it.kq == 2;
             switch (it.kp) {
             case 8:
-                ok = knn_cull_unit<8, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
-                                                it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
-                                                ktile, ts, order, nullptr, cs);
+                if (q2)
+                    AIDW_CULL_UNIT(8, 2);
+                else
+                    AIDW_CULL_UNIT(8, 4);
                 break;
             case 12:
-                ok = knn_cull_unit<12, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
-                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
-                                                 ktile, ts, order, nullptr, cs);
+                if (q2)
+                    AIDW_CULL_UNIT(12, 2);
+                else
+                    AIDW_CULL_UNIT(12, 4);
                 break;
             case 16:
-                ok = knn_cull_unit<16, 4, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
-                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
-                                                 ktile, ts, order, nullptr, cs);
+                if (q2)
+                    AIDW_CULL_UNIT(16, 2);
+                else
+                    AIDW_CULL_UNIT(16, 4);
                 break;
             default:
-                ok = knn_cull_unit<32, 2, false>(it.ds, it.m, qbase, it.ntiles, it.ntiles_p2,
-                                                 it.sqx, it.sqy, it.k, it.part_d2, nullptr, err,
-                                                 ktile, ts, order, nullptr, cs);
+                AIDW_CULL_UNIT(32, 2);
                 break;
             }
+#undef AIDW_CULL_UNIT
             if (ok)
                 cta_publish(&it.cnt_knn[wu.qblock]);
         } else if (wu.type == kUnitSelect) {
@@ -293,17 +300,19 @@ int batch_grid(int sm_count, size_t dyn, int qw, int ctas_per_sm)
 
 // Phase-1 plan of a batch item: one pruned unit per query block when the dataset's tile order
 // fits in shared memory, else split scans.
-PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, bool *cull)
+PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, int kq, bool *cull)
 {
     *cull = n_pad / kTileF32Knn <= kMaxCullTiles;
-    const int qk = kThreads * (kp <= 16 ? 4 : 2);
+    const int qk = kThreads * (*cull ? kq : (kp <= 16 ? 4 : 2));
     return batch_pass(m, n_pad, qk, *cull ? n_pad : kBatchKnnSplit);
 }
 
 size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config &cfg)
 {
     bool cull;
-    const PassPlan pk = batch_knn_plan(m, n_pad, kp_for(k, cfg.knn_list), &cull);
+    const int kp = kp_for(k, cfg.knn_list);
+    const PassPlan pk = batch_knn_plan(m, n_pad, kp, cull_queries_per_thread(kp,
+                                       cfg.knn_queries_per_thread), &cull);
     const PassPlan pw = batch_pass(m, n_pad, kThreads * cfg.queries_per_thread,
                                    cfg.split_points);
     const size_t mm = static_cast<size_t>(m);
@@ -353,10 +362,11 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.m = b.m;
         d.k = b.params.k;
         d.kp = kp_for(b.params.k, cfg.knn_list);
+        d.kq = cull_queries_per_thread(d.kp, cfg.knn_queries_per_thread);
         d.r_exp = r_exp;
         d.am = alpha_map(b.params);
         bool cull;
-        d.knn = batch_knn_plan(b.m, dev.n_pad, d.kp, &cull);
+        d.knn = batch_knn_plan(b.m, dev.n_pad, d.kp, d.kq, &cull);
         d.w = batch_pass(b.m, dev.n_pad, kThreads * cfg.queries_per_thread, cfg.split_points);
         d.ntiles = static_cast<int32_t>(dev.n_pad / kTileF32Knn);
         int p2 = 1;

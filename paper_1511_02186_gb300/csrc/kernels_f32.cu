@@ -86,11 +86,10 @@ f32_finalize_kernel(int64_t m, int S, const float *__restrict__ part_sum,
         out[perm ? perm[q] : q] = finalize_query(q, m, S, part_sum);
 }
 
-template <int KP, bool IDX>
+template <int KP, int Q, bool IDX>
 cudaError_t launch_cull_t(const DatasetDev &ds, const Plan &pl, const float *sqx,
                           const float *sqy, int k, const Scratch &sc, int *err, cudaStream_t st)
 {
-    constexpr int Q = knn_q<KP>();
     const int ntiles = static_cast<int>(ds.n_pad / kTileF32Knn);
     int p2 = 1;
     while (p2 < ntiles)
@@ -223,20 +222,27 @@ cudaError_t launch_f32_knn_cull(const DatasetDev &ds, const Plan &pl, const floa
                                 const float *sqy, int k, const Scratch &sc, int *err,
                                 cudaStream_t st)
 {
+    const bool q2 = pl.kq == 2;
+#define AIDW_CULL(KP, Q)                                                                       \
+    return pl.with_idx ? launch_cull_t<KP, Q, true>(ds, pl, sqx, sqy, k, sc, err, st)         \
+                       : launch_cull_t<KP, Q, false>(ds, pl, sqx, sqy, k, sc, err, st)
     switch (pl.kp) {
     case 8:
-        return pl.with_idx ? launch_cull_t<8, true>(ds, pl, sqx, sqy, k, sc, err, st)
-                           : launch_cull_t<8, false>(ds, pl, sqx, sqy, k, sc, err, st);
+        if (q2)
+            AIDW_CULL(8, 2);
+        AIDW_CULL(8, 4);
     case 12:
-        return pl.with_idx ? launch_cull_t<12, true>(ds, pl, sqx, sqy, k, sc, err, st)
-                           : launch_cull_t<12, false>(ds, pl, sqx, sqy, k, sc, err, st);
+        if (q2)
+            AIDW_CULL(12, 2);
+        AIDW_CULL(12, 4);
     case 16:
-        return pl.with_idx ? launch_cull_t<16, true>(ds, pl, sqx, sqy, k, sc, err, st)
-                           : launch_cull_t<16, false>(ds, pl, sqx, sqy, k, sc, err, st);
+        if (q2)
+            AIDW_CULL(16, 2);
+        AIDW_CULL(16, 4);
     default:
-        return pl.with_idx ? launch_cull_t<32, true>(ds, pl, sqx, sqy, k, sc, err, st)
-                           : launch_cull_t<32, false>(ds, pl, sqx, sqy, k, sc, err, st);
+        AIDW_CULL(32, 2);
     }
+#undef AIDW_CULL
 }
 
 cudaError_t launch_f32_weights(const DatasetDev &ds, const Plan &pl, const float *qx,

@@ -21,7 +21,9 @@ NEUTRAL = [
     dict(tile_points=256),
     dict(knn_list=16),
     dict(knn_list=32),
+    dict(knn_queries_per_thread=2),
     dict(queries_per_thread=8, tile_points=256, knn_list=32, ctas_per_sm=2),
+    dict(queries_per_thread=2, knn_queries_per_thread=2, knn_list=16),
 ]
 
 
