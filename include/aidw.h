@@ -139,8 +139,8 @@ int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int
  * Limit: about m * (4k + 24) bytes must fit in 16 MiB (m <= 262,144 for k = 10, about
  * 110,000 for k = 32); larger calls return AIDW_ERR_INVALID_ARG. The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress), so make that first call before
- * any stream capture. All calls share the one array: calls whose work overlaps on the GPU (for example
- * on two streams) race and must be serialised by the caller. Stream-ordered on `stream`;
+ * any stream capture. All calls share the one array: calls whose work overlaps on the GPU (for
+ * example on two streams) race and must be serialised by the caller. Stream-ordered on `stream`;
  * kernel timeouts are reported by aidw_check_device_errors. */
 int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, const float *qy,
                              int64_t m, const aidw_params *p, float *out, void *stream);
@@ -240,9 +240,9 @@ int aidw_get_tune_config(aidw_ctx *ctx, aidw_tune_config *out);
 /* Times an FP32 interpolation (arguments as aidw_interpolate, device arrays only) under
  * candidate shapes by coordinate search from the context's shape (queries per thread, tile
  * points, k-list length, phase-1 queries per thread; each candidate run `reps` times after one
- * warm-up, fastest run counts) and returns the fastest in *best with its time in *best_ms. `out` receives the
- * results of the last run. Synchronous. Errors: as aidw_interpolate; INVALID_ARG for host
- * arrays, F64 or reps < 1. */
+ * warm-up, fastest run counts) and returns the fastest in *best with its time in *best_ms.
+ * `out` receives the results of the last run. Synchronous. Errors: as aidw_interpolate;
+ * INVALID_ARG for host arrays, F64 or reps < 1. */
 int aidw_autotune_interpolate(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy,
                               int64_t m, const aidw_params *p, void *out, int32_t reps,
                               uint32_t flags, aidw_tune_config *best, double *best_ms);

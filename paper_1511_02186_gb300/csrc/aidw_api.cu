@@ -780,10 +780,11 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     const int64_t n_pad = (n + kPadPoints - 1) / kPadPoints * kPadPoints;
     const size_t np = static_cast<size_t>(n_pad);
     const int64_t ntiles = n_pad / kTileF32Knn;
+    const int64_t nsub = n_pad / kSubTile;
     const size_t bytes = align256(np * sizeof(float4)) + align256(np * sizeof(float2)) +
                          align256(np * sizeof(int32_t)) + align256(np * sizeof(double2)) +
-                         align256(np * sizeof(double)) +
-                         align256(ntiles * sizeof(float4)) + align256(sizeof(float4));
+                         align256(np * sizeof(double)) + align256(ntiles * sizeof(float4)) +
+                         align256(nsub * sizeof(float4)) + align256(sizeof(float4));
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         if (ctx->fail_after >= 0) {
@@ -863,6 +864,8 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     b += align256(np * sizeof(double));
     float4 *tbox = reinterpret_cast<float4 *>(b);
     b += align256(ntiles * sizeof(float4));
+    float4 *sbox = reinterpret_cast<float4 *>(b);
+    b += align256(nsub * sizeof(float4));
     float4 *box = reinterpret_cast<float4 *>(b);
 
     int rc = AIDW_OK;
@@ -895,6 +898,7 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
             ok = cudaGetLastError() == cudaSuccess;
         }
         ok = ok && tile_boxes(nxy2, ntiles, tbox, 0) == cudaSuccess;
+        ok = ok && sub_tile_boxes(nxy2, nsub, sbox, 0) == cudaSuccess;
         ok = ok && cudaDeviceSynchronize() == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -912,6 +916,7 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     rec.dev.zz = zz;
     rec.dev.orig = orig;
     rec.dev.tile_box = tbox;
+    rec.dev.sub_box = sbox;
     rec.dev.box = box;
     rec.dev.xy64 = xy64;
     rec.dev.z64 = z64;

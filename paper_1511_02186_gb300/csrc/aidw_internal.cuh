@@ -17,6 +17,7 @@ constexpr int kTileF32W = 512;     // float4 (-x, -x, -y, -y) + float2 (z, z): 1
 constexpr int kTileF64Knn = 512;   // double2 (x, y): 8 KiB per buffer
 constexpr int kTileF64W = 512;     // double2 + double: 12 KiB per buffer
 constexpr int kPadPoints = 2048;   // common multiple of every tile and split granule
+constexpr int kSubTile = 64;       // points per sub-tile box (pruned phase 1)
 
 // Added under the square of distances: it is absorbed (below half an ulp) for any distance
 // above ~1e-15 of unit scale, and turns an exact coincidence (d2 == 0) into d2 == kEps so
@@ -55,6 +56,7 @@ struct DatasetDev {
     const float2 *zz;       // [n_pad] (z, z), Z-order
     const int32_t *orig;    // [n_pad] caller's index of each stored point, -1 for padding
     const float4 *tile_box; // [n_pad / kTileF32Knn] (xmin, ymin, xmax, ymax) of finite points
+    const float4 *sub_box;  // [n_pad / kSubTile] the same per 64-point sub-tile
     const float4 *box;      // [1] bounding box of all points
     const double2 *xy64;    // [n_pad] caller's order
     const double *z64;      // [n_pad] caller's order
@@ -135,6 +137,7 @@ cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_
                         int64_t n_total, const float4 *box, uint32_t *keys, uint32_t *vals,
                         cudaStream_t st);
 cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st);
+cudaError_t sub_tile_boxes(const float4 *nxy2, int64_t nsub, float4 *boxes, cudaStream_t st);
 cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
                            float *sqx, float *sqy, cudaStream_t st);
 cudaError_t morton_keys_f64(const double *x, const double *y, int64_t n, const float4 *box,

@@ -56,7 +56,7 @@ bool same(const aidw_tune_config &a, const aidw_tune_config &b)
            a.knn_queries_per_thread == b.knn_queries_per_thread;
 }
 
-// ---- process-wide cache -----------------------------------------------------------------------
+// ---- process-wide cache ----------------------------------------------------------------------
 
 struct CacheEntry {
     aidw_tune_config cfg;
@@ -113,7 +113,7 @@ bool blank(const char *s)
     return true;
 }
 
-// ---- workload keys ------------------------------------------------------------------------------
+// ---- workload keys ---------------------------------------------------------------------------
 
 int log2_round(double v)
 {
@@ -130,7 +130,7 @@ std::string device_tag(aidw_ctx *ctx)
     return b;
 }
 
-// ---- timing --------------------------------------------------------------------------------------
+// ---- timing ----------------------------------------------------------------------------------
 
 struct Timer {
     cudaStream_t st = nullptr;

@@ -19,6 +19,7 @@ namespace f32dev {
 constexpr int kChunkKnn = 8;  // points between neighbour-list threshold checks
 constexpr int kChunkW = 32;   // points summed in plain FP32 before a Kahan merge
 constexpr float kFilterMargin = 1.0f + 9.5367431640625e-07f;  // 1 + 2^-20
+constexpr float kBoundShrink = 1.0f - 9.5367431640625e-07f;   // 1 - 2^-20, box bounds
 
 // Squared distance from negated data coordinates: q + (-p) is exactly q - p.
 __device__ __forceinline__ float dist2_neg(float qx, float qy, float npx, float npy)
@@ -86,15 +87,36 @@ __device__ __forceinline__ void drain(TileSeq &ts, int t, int ntiles)
 }
 
 // One tile of kTileF32Knn points (stored positions pbase..) through the phase-1 filter and,
-// where a sign bit fires, the exact insertion (see knn_unit).
+// where a sign bit fires, the exact insertion (see knn_unit). With `sub` (the tile's 64-point
+// sub-tile boxes) the warp skips a sub-tile when, for every one of its queries, the box bound
+// (shrunk by 2^-20 for rounding, as for tiles) exceeds the query's current k-th distance.
 template <int KP, int Q, bool IDX>
 __device__ __forceinline__ void knn_tile(const float4 *tb, int64_t pbase, float2 (&qxp)[Q / 2],
                                          float2 (&qyp)[Q / 2], float2 (&nthr)[Q / 2],
-                                         float (&L)[Q][KP], int32_t *idx_smem)
+                                         float (&L)[Q][KP], int32_t *idx_smem,
+                                         const float4 *__restrict__ sub = nullptr)
 {
     constexpr int H = Q / 2;
+    static_assert(kSubTile % kChunkKnn == 0 && kTileF32Knn % kSubTile == 0, "whole sub-tiles");
     const int tid = threadIdx.x;
     for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
+        if (sub && (c % kSubTile) == 0) {
+            const float4 sb = sub[c / kSubTile];
+            bool need = false;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const float qx = (j & 1) ? qxp[j / 2].y : qxp[j / 2].x;
+                const float qy = (j & 1) ? qyp[j / 2].y : qyp[j / 2].x;
+                const float dx = fmaxf(0.0f, fmaxf(sb.x - qx, qx - sb.z));
+                const float dy = fmaxf(0.0f, fmaxf(sb.y - qy, qy - sb.w));
+                const float lb = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), kBoundShrink);
+                need |= !(lb > L[j][KP - 1]);
+            }
+            if (!__any_sync(0xffffffffu, need)) {
+                c += kSubTile - kChunkKnn;  // the loop adds the last chunk
+                continue;
+            }
+        }
         uint32_t acc[Q];
 #pragma unroll
         for (int j = 0; j < Q; ++j)
@@ -263,7 +285,6 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
 // list: its exact FP32 distance is at least the box bound (the bound is shrunk by 2^-20 to
 // cover rounding), which exceeds every query's current k-th distance.
 // ---------------------------------------------------------------------------------------------
-constexpr float kBoundShrink = 1.0f - 9.5367431640625e-07f;  // 1 - 2^-20
 
 // Shared-memory scratch of a pruned phase-1 unit.
 struct CullShared {
@@ -426,7 +447,8 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
         const float wdy = fmaxf(0.0f, fmaxf(tb.y - wb.w, wb.y - tb.w));
         const float wlb = __fmul_rn(__fmaf_rn(wdx, wdx, __fmul_rn(wdy, wdy)), kBoundShrink);
         if (!(wlb > wthr))
-            knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem);
+            knn_tile<KP, Q, IDX>(tile[b], t * kTileF32Knn, qxp, qyp, nthr, L, idx_smem,
+                                 ds.sub_box + t * (kTileF32Knn / kSubTile));
         float mx = -CUDART_INF_F;
 #pragma unroll
         for (int j = 0; j < Q; ++j)

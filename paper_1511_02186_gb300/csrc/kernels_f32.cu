@@ -182,7 +182,8 @@ int w_slots_t()
 int f32_w_slots_per_sm(int qw, int tw)
 {
     if (tw == 256)
-        return qw == 2 ? w_slots_t<2, 256>() : (qw == 8 ? w_slots_t<8, 256>() : w_slots_t<4, 256>());
+        return qw == 2 ? w_slots_t<2, 256>()
+                       : (qw == 8 ? w_slots_t<8, 256>() : w_slots_t<4, 256>());
     return qw == 2 ? w_slots_t<2, 512>() : (qw == 8 ? w_slots_t<8, 512>() : w_slots_t<4, 512>());
 }
 

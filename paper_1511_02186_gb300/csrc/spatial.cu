@@ -176,6 +176,9 @@ radix_scatter_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restric
 }
 
 // One warp per tile of kTileF32Knn sorted points: box of the finite points.
+// Bounding box of the finite points of every group of G consecutive stored points (one warp
+// per group).
+template <int G>
 __global__ void tile_box_kernel(const float4 *__restrict__ nxy2, int64_t ntiles, float4 *boxes)
 {
     const int64_t t = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -183,8 +186,8 @@ __global__ void tile_box_kernel(const float4 *__restrict__ nxy2, int64_t ntiles,
     if (t >= ntiles)
         return;
     float x0 = CUDART_INF_F, y0 = CUDART_INF_F, x1 = -CUDART_INF_F, y1 = -CUDART_INF_F;
-    for (int u = lane; u < kTileF32Knn; u += 32) {
-        const float4 p = nxy2[t * kTileF32Knn + u];
+    for (int u = lane; u < G; u += 32) {
+        const float4 p = nxy2[t * G + u];
         const float px = -p.x, py = -p.z;
         if (isfinite(px) && isfinite(py)) {
             x0 = fminf(x0, px);
@@ -297,7 +300,15 @@ cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_
 
 cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st)
 {
-    tile_box_kernel<<<grid_for(ntiles * 32, 256, 1 << 20), 256, 0, st>>>(nxy2, ntiles, boxes);
+    tile_box_kernel<kTileF32Knn>
+        <<<grid_for(ntiles * 32, 256, 1 << 20), 256, 0, st>>>(nxy2, ntiles, boxes);
+    return cudaGetLastError();
+}
+
+cudaError_t sub_tile_boxes(const float4 *nxy2, int64_t nsub, float4 *boxes, cudaStream_t st)
+{
+    tile_box_kernel<kSubTile><<<grid_for(nsub * 32, 256, 1 << 20), 256, 0, st>>>(nxy2, nsub,
+                                                                                 boxes);
     return cudaGetLastError();
 }
 
