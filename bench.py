@@ -506,13 +506,17 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     __graft_entry__.build()
-    wl = workloads.uniform_paper(0, n=args.n, m=args.n)
+    wl = workloads.uniform_paper(0, n=args.n, m=args.m or args.n)
     ctx = aidw.Context(local)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
-    qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)
-    qy = torch.as_tensor(wl.qy, dtype=torch.float32, device=dev)
-    out = torch.empty(wl.m, dtype=torch.float32, device=dev)
-    p = aidw.default_params(k=wl.k, levels=wl.levels)
+    f64 = args.precision == "f64"
+    if f64 and args.extras:
+        raise SystemExit("--precision f64 is a profiling option: use it with --no-extras")
+    qdt = torch.float64 if f64 else torch.float32
+    qx = torch.as_tensor(wl.qx, dtype=qdt, device=dev)
+    qy = torch.as_tensor(wl.qy, dtype=qdt, device=dev)
+    out = torch.empty(wl.m, dtype=qdt, device=dev)
+    p = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64 if f64 else aidw.F32C)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -581,9 +585,10 @@ def run_gpu(args):
         ds.destroy()
         ctx.close()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            metric = METRIC if not f64 else "AIDW pair-evals/s (FP64 path)"
+            print(json.dumps({"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup,
-                              "config": workload_config(wl),
+                              "config": workload_config(wl), "precision": args.precision,
                               "kernel_ms": {"knn": kn, "select": ks, "weights": kw,
                                             "finalize": kf},
                               "note": "profiling run without the extra measurements"}))
@@ -709,6 +714,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=N_DATA,
                     help="data and query count (smaller sizes only for profiling runs)")
+    ap.add_argument("--m", type=int, default=0,
+                    help="query count (default: --n; smaller sizes only for profiling runs)")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
+                    help="path of the timed step (f64 only with --no-extras, for profiling)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the FP64, end-to-end and CPU-baseline measurements")
     args = ap.parse_args()
