@@ -38,6 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # bounding-box bounds), so it has no per-pair minimum; a step's n * m pair-evaluations are bound
 # by phase 2.
 FP32_OPS_P2, MUFU_OPS_P2 = 7, 2
+FP64_OPS_P2 = 31  # FP64 instructions per pair in the FP64 phase-2 kernel
+FP64_PIPE_PER_CLK_SM = 2.0  # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 DFMA per clk per SM
 LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
 
 
@@ -602,11 +604,19 @@ def run_gpu(args):
     p64 = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64)
     ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_profiling(True)
     e0.record(stream)
     ctx.interpolate(ds, qx64, qy64, p64, stream=stream.cuda_stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    kt64 = ctx.kernel_times()
+    ctx.set_profiling(False)
     fp64_rate = q64 * wl.n / (e0.elapsed_time(e1) / 1e3)
+    # FP64 phase 2 against the FP64 pipe: FP64 instructions per pair of the kernel as written
+    # (distance 4, table log2 13, power scale 1, table exp2 11, sums 2) at 2 per clock per SM,
+    # GB300's nominal FP64 rate (1.25 TFLOP/s) and the pipe's peak that ncu reports.
+    fp64_w_achieved = q64 * wl.n / (kt64.weights_ms / 1e3)
+    fp64_w_peak = sm * clk_hz * FP64_PIPE_PER_CLK_SM / FP64_OPS_P2
 
     # End to end through the public API with host buffers: dataset upload (FP64 host arrays),
     # query upload from pinned memory, interpolation, result download.
@@ -667,12 +677,25 @@ def run_gpu(args):
                          "step_note": "whole step (all kernels incl. query ordering and the "
                                       "pruned phase 1) against the phase-2 bound"},
             "pipe_rates": {"ffma_per_clk_sm": rates.ffma_per_clk_sm,
+                           "dfma_per_clk_sm": rates.dfma_per_clk_sm,
                            "ex2_per_clk_sm": rates.ex2_per_clk_sm,
                            "lg2_per_clk_sm": rates.lg2_per_clk_sm,
                            "fmnmx_per_clk_sm": rates.fmnmx_per_clk_sm,
                            "probe_sm_mhz": rates.sm_clock_mhz},
             "fp64_path": {"value": fp64_rate, "unit": UNIT,
-                          "sample": f"{q64} seeded queries x all {wl.n} data points"},
+                          "sample": f"{q64} seeded queries x all {wl.n} data points",
+                          "kernel_ms": {"knn": kt64.knn_ms, "select": kt64.select_ms,
+                                        "weights": kt64.weights_ms,
+                                        "finalize": kt64.finalize_ms},
+                          "roofline": {"bound": "fp64", "kernel": "f64_weights_kernel",
+                                       "achieved": fp64_w_achieved, "peak": fp64_w_peak,
+                                       "unit": UNIT, "frac": fp64_w_achieved / fp64_w_peak,
+                                       "peak_basis": (f"{sm} SMs x {sm_mhz_peak:.0f} MHz x "
+                                                      f"{FP64_PIPE_PER_CLK_SM:g} FP64 "
+                                                      "instructions per clk per SM (nominal "
+                                                      "1.25 TFLOP/s; ncu's FP64 pipe peak) / "
+                                                      f"{FP64_OPS_P2} FP64 instructions per "
+                                                      "pair")}},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "includes": "dataset upload + conversion, query upload, both phases, "

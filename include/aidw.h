@@ -349,8 +349,8 @@ int aidw_set_profiling(aidw_ctx *ctx, int on);
 int aidw_last_kernel_times(aidw_ctx *ctx, aidw_kernel_times *out);
 
 /* Measured issue rates of the pipes that bound the kernels, for roofline denominators:
- * FP32 FFMA and MUFU ex2/lg2 results per clock per SM, timed by microbenchmark kernels on the
- * context's device, plus the SM count and the SM clock the driver reports. */
+ * FP32 FFMA, MUFU ex2/lg2 and FP64 DFMA results per clock per SM, timed by microbenchmark
+ * kernels on the context's device, plus the SM count and the SM clock the driver reports. */
 typedef struct aidw_pipe_rates {
     double ffma_per_clk_sm;
     double ex2_per_clk_sm;
@@ -359,6 +359,7 @@ typedef struct aidw_pipe_rates {
     double sm_clock_mhz; /* clock observed during the microbenchmarks */
     int32_t sm_count;
     int32_t reserved;
+    double dfma_per_clk_sm; /* FP64 fused multiply-adds per clock per SM */
 } aidw_pipe_rates;
 
 int aidw_measure_pipe_rates(aidw_ctx *ctx, aidw_pipe_rates *out);

@@ -66,7 +66,7 @@ class PipeRates(ctypes.Structure):
     _fields_ = [("ffma_per_clk_sm", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
                 ("lg2_per_clk_sm", ctypes.c_double), ("fmnmx_per_clk_sm", ctypes.c_double),
                 ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("dfma_per_clk_sm", ctypes.c_double)]
 
 
 class ServingStats(ctypes.Structure):

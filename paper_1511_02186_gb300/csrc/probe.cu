@@ -1,5 +1,5 @@
-// Microbenchmarks of the pipes that bound the AIDW scans: FP32 FFMA, MUFU ex2 and lg2, and
-// FMNMX. Each kernel runs many independent dependency chains per thread on every SM and
+// Microbenchmarks of the pipes that bound the AIDW scans: FP32 FFMA, MUFU ex2 and lg2, FMNMX,
+// and FP64 DFMA. Each kernel runs many independent dependency chains per thread on every SM and
 // records its own SM clock ticks and global-timer nanoseconds, so the result is in
 // instructions per clock per SM and the observed clock is reported beside it.
 #include <algorithm>
@@ -61,13 +61,47 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seed, float 
         times[blockIdx.x] = ProbeTimes{c0, c1, n0, n1};
 }
 
+// FP64 FMA chains (the pipe that bounds the FP64 path).
+__global__ void __launch_bounds__(kProbeThreads) probe_dfma_kernel(double seed, double *sink,
+                                                                   ProbeTimes *times)
+{
+    double v[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        v[c] = seed + 0.001 * (threadIdx.x + c);
+    const double a = seed * 0.5, b = 1.0 - seed;
+    __syncthreads();
+    const unsigned long long c0 = clock64(), n0 = global_ns();
+    for (int i = 0; i < kIters / 8; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            v[c] = __fma_rn(v[c], a, b);
+    }
+    __syncthreads();
+    const unsigned long long c1 = clock64(), n1 = global_ns();
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        s += v[c];
+    if (s == 12345.678)
+        *sink = s;
+    if (threadIdx.x == 0)
+        times[blockIdx.x] = ProbeTimes{c0, c1, n0, n1};
+}
+
 template <int OP>
 cudaError_t run_one(int sm_count, int blocks_per_sm, float *sink, ProbeTimes *d_times,
                     double *per_clk_sm, double *mhz)
 {
     const int blocks = sm_count * blocks_per_sm;
-    probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);  // warm-up
-    probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);
+    if (OP == 4) {
+        double *dsink = reinterpret_cast<double *>(sink);
+        probe_dfma_kernel<<<blocks, kProbeThreads>>>(0.37, dsink, d_times);  // warm-up
+        probe_dfma_kernel<<<blocks, kProbeThreads>>>(0.37, dsink, d_times);
+    } else {
+        probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);  // warm-up
+        probe_kernel<OP><<<blocks, kProbeThreads>>>(0.37f, sink, d_times);
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess)
         return e;
@@ -86,7 +120,8 @@ cudaError_t run_one(int sm_count, int blocks_per_sm, float *sink, ProbeTimes *d_
     std::sort(clk.begin(), clk.end());
     std::sort(mh.begin(), mh.end());
     const double span = clk[blocks / 2];
-    const double ops_per_sm = static_cast<double>(blocks_per_sm) * kProbeThreads * kIters * kChains;
+    const double iters = OP == 4 ? kIters / 8 : kIters;
+    const double ops_per_sm = static_cast<double>(blocks_per_sm) * kProbeThreads * iters * kChains;
     *per_clk_sm = ops_per_sm / span;
     *mhz = mh[blocks / 2];
     return cudaSuccess;
@@ -99,7 +134,7 @@ cudaError_t run_pipe_probe(int sm_count, aidw_pipe_rates *out)
     float *sink = nullptr;
     ProbeTimes *d_times = nullptr;
     const int bps = 2;  // 2 x 512 threads: 32 warps per SM
-    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    cudaError_t e = cudaMalloc(&sink, sizeof(double));
     if (e == cudaSuccess)
         e = cudaMalloc(&d_times, sizeof(ProbeTimes) * sm_count * bps);
     double mhz[4] = {};
@@ -111,6 +146,9 @@ cudaError_t run_pipe_probe(int sm_count, aidw_pipe_rates *out)
         e = run_one<2>(sm_count, bps, sink, d_times, &out->lg2_per_clk_sm, &mhz[2]);
     if (e == cudaSuccess)
         e = run_one<3>(sm_count, bps, sink, d_times, &out->fmnmx_per_clk_sm, &mhz[3]);
+    double mhz64 = 0.0;
+    if (e == cudaSuccess)
+        e = run_one<4>(sm_count, bps, sink, d_times, &out->dfma_per_clk_sm, &mhz64);
     out->sm_clock_mhz = (mhz[0] + mhz[1] + mhz[2] + mhz[3]) / 4.0;
     out->sm_count = sm_count;
     out->reserved = 0;

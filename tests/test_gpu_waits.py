@@ -39,3 +39,15 @@ def test_expire_wait_rejects_bad_arguments():
             with pytest.raises(aidw.AidwError):
                 ctx.expire_wait(which, polls)
         assert ctx.check_device_errors() == aidw.OK
+
+
+def test_pipe_rate_probes_are_plausible():
+    """The microbenchmarks behind the roofline denominators: every rate positive and below the
+    SM's lane count, SM clock in a GB300 range."""
+    with aidw.Context(0) as ctx:
+        r = ctx.pipe_rates()
+        assert r.sm_count > 0 and 500.0 < r.sm_clock_mhz < 3000.0
+        for v in (r.ffma_per_clk_sm, r.ex2_per_clk_sm, r.lg2_per_clk_sm, r.fmnmx_per_clk_sm,
+                  r.dfma_per_clk_sm):
+            assert 0.0 < v <= 512.0
+        assert r.lg2_per_clk_sm <= r.ffma_per_clk_sm and r.dfma_per_clk_sm <= r.ffma_per_clk_sm
