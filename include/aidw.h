@@ -215,11 +215,16 @@ typedef struct aidw_tune_config {
     int32_t knn_queries_per_thread; /* pruned phase 1: 2 or 4 queries per thread (query block
                                  * 128x), 0 = 4 for lists of up to 16, else 2; lists of 32
                                  * always take 2 */
-    int32_t reserved[2];        /* zero */
+    int32_t unit_order;         /* batches: 0 = all phase-1 units, then all phase-2 units;
+                                 * 1 = phase-2 units of each item interleaved with phase-1
+                                 * units of items further down the list (both phases run on
+                                 * the SMs at once) */
+    int32_t reserved;           /* zero */
 } aidw_tune_config;
 
 /* Fills the built-in shape: 4 queries per thread, 512-point tiles, the smallest list, 65,536
- * points per batch work unit, full occupancy, phase-1 queries per thread by list length. */
+ * points per batch work unit, full occupancy, phase-1 queries per thread by list length,
+ * phase-by-phase unit order. */
 int aidw_tune_config_default(aidw_tune_config *out);
 /* AIDW_OK if every field is one of the values above, else AIDW_ERR_INVALID_ARG. */
 int aidw_tune_config_check(const aidw_tune_config *cfg);
@@ -253,7 +258,7 @@ int aidw_batch_get_config(aidw_ctx *ctx, aidw_batch *batch, aidw_tune_config *ou
 
 /* Times the prepared batch under candidate shapes by coordinate search from its current one
  * (queries per thread, tile points, k-list length, phase-1 queries per thread, points per work
- * unit, CTAs per SM; each
+ * unit, CTAs per SM, unit order; each
  * candidate launched `reps` times after one warm-up, fastest launch counts), leaves the batch
  * prepared with the fastest and returns it. Synchronous; after a search the batch's outputs
  * hold the winner's results. Errors: INVALID_ARG, NOT_FOUND (a dataset was destroyed), OOM,
@@ -265,7 +270,8 @@ int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *batch, int32_t reps, uint32_t
  * characters; the autotuner's keys name the device and the workload's size class) mapped to
  * shapes. Files hold one JSON object per line:
  *   {"key": "...", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
- *    "split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "ms": 91.5}
+ *    "split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "unit_order": 0,
+ *    "ms": 91.5}
  * _load merges a file into the cache (INVALID_ARG on a malformed line, NOT_FOUND if the file
  * cannot be opened; nothing is merged on error); _save writes the whole cache; _get returns
  * NOT_FOUND for an unknown key. Host only: usable without a GPU. */

@@ -87,14 +87,14 @@ class BatchItem(ctypes.Structure):
 class TuneConfig(ctypes.Structure):
     """``aidw_tune_config``: kernel shape (phase-2 queries per thread and tile points, k-list
     length, points per batched phase-2 unit, persistent CTAs per SM, phase-1 queries per
-    thread)."""
+    thread, batch unit order)."""
     _fields_ = [("queries_per_thread", ctypes.c_int32), ("tile_points", ctypes.c_int32),
                 ("knn_list", ctypes.c_int32), ("split_points", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("knn_queries_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("unit_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     FIELDS = ("queries_per_thread", "tile_points", "knn_list", "split_points", "ctas_per_sm",
-              "knn_queries_per_thread")
+              "knn_queries_per_thread", "unit_order")
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f in self.FIELDS}

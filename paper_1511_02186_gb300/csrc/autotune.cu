@@ -29,6 +29,7 @@ aidw_tune_config tune_default()
     c.split_points = 65536;
     c.ctas_per_sm = 0;
     c.knn_queries_per_thread = 0;
+    c.unit_order = 0;
     return c;
 }
 
@@ -43,7 +44,8 @@ bool tune_valid(const aidw_tune_config &c)
     const bool ct = c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
     const bool kq = c.knn_queries_per_thread == 0 || c.knn_queries_per_thread == 2 ||
                     c.knn_queries_per_thread == 4;
-    return qw && tw && kl && sp && ct && kq && c.reserved[0] == 0 && c.reserved[1] == 0;
+    const bool uo = c.unit_order == 0 || c.unit_order == 1;
+    return qw && tw && kl && sp && ct && kq && uo && c.reserved == 0;
 }
 
 namespace {
@@ -53,7 +55,8 @@ bool same(const aidw_tune_config &a, const aidw_tune_config &b)
     return a.queries_per_thread == b.queries_per_thread && a.tile_points == b.tile_points &&
            a.knn_list == b.knn_list && a.split_points == b.split_points &&
            a.ctas_per_sm == b.ctas_per_sm &&
-           a.knn_queries_per_thread == b.knn_queries_per_thread;
+           a.knn_queries_per_thread == b.knn_queries_per_thread &&
+           a.unit_order == b.unit_order;
 }
 
 // ---- process-wide cache ----------------------------------------------------------------------
@@ -92,10 +95,10 @@ bool parse_line(const char *line, std::string *key, CacheEntry *e)
         line,
         " { \"key\" : \"%255[^\"]\" , \"queries_per_thread\" : %d , \"tile_points\" : %d , "
         "\"knn_list\" : %d , \"split_points\" : %d , \"ctas_per_sm\" : %d , "
-        "\"knn_queries_per_thread\" : %d , \"ms\" : %lf } %n",
+        "\"knn_queries_per_thread\" : %d , \"unit_order\" : %d , \"ms\" : %lf } %n",
         kbuf, &c.queries_per_thread, &c.tile_points, &c.knn_list, &c.split_points,
-        &c.ctas_per_sm, &c.knn_queries_per_thread, &ms, &used);
-    if (got != 8 || used < 0 || line[used] != '\0')
+        &c.ctas_per_sm, &c.knn_queries_per_thread, &c.unit_order, &ms, &used);
+    if (got != 9 || used < 0 || line[used] != '\0')
         return false;
     if (!key_valid(kbuf) || !tune_valid(c) || !std::isfinite(ms))
         return false;
@@ -278,10 +281,11 @@ int aidw_tune_cache_save(const char *path)
             ok &= std::fprintf(f,
                                "{\"key\": \"%s\", \"queries_per_thread\": %d, \"tile_points\": "
                                "%d, \"knn_list\": %d, \"split_points\": %d, \"ctas_per_sm\": %d, "
-                               "\"knn_queries_per_thread\": %d, \"ms\": %.6f}\n",
+                               "\"knn_queries_per_thread\": %d, \"unit_order\": %d, "
+                               "\"ms\": %.6f}\n",
                                kv.first.c_str(), c.queries_per_thread, c.tile_points,
                                c.knn_list, c.split_points, c.ctas_per_sm,
-                               c.knn_queries_per_thread, kv.second.ms) > 0;
+                               c.knn_queries_per_thread, c.unit_order, kv.second.ms) > 0;
         }
     }
     ok &= std::fclose(f) == 0;
@@ -486,7 +490,7 @@ int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *b, int32_t reps, uint32_t fla
             // The same kernels for every item as the shape already timed: nothing to time.
             if (c.queries_per_thread != bb.queries_per_thread ||
                 c.tile_points != bb.tile_points || c.split_points != bb.split_points ||
-                c.ctas_per_sm != bb.ctas_per_sm)
+                c.ctas_per_sm != bb.ctas_per_sm || c.unit_order != bb.unit_order)
                 return false;
             for (const aidw_batch_item &it : b->items) {
                 const int kc = f32_list_length(it.params.k, c.knn_list);
@@ -502,6 +506,7 @@ int aidw_batch_autotune(aidw_ctx *ctx, aidw_batch *b, int32_t reps, uint32_t fla
             {&aidw_tune_config::tile_points, {256, 512}},
             {&aidw_tune_config::knn_list, {0, 16, 32}},
             {&aidw_tune_config::knn_queries_per_thread, {0, 2, 4}},
+            {&aidw_tune_config::unit_order, {0, 1}},
             {&aidw_tune_config::split_points, {16384, 32768, 65536, 131072, 262144}},
             {&aidw_tune_config::ctas_per_sm, ctas},
         };

@@ -15,10 +15,12 @@
 // keys over each item's dataset box, a stable radix sort by key, then a stable sort by item) so
 // that each KNN unit's block is compact; results go back to the caller's order.
 // The work list holds all KNN units, then all SELECT, WEIGHTS and FINAL units, each phase in
-// decreasing item size; CTAs take units in list order from one atomic counter. A unit only
-// waits on units earlier in the list, which running CTAs have already taken and never block
-// on later ones, so the waits end; each wait is still bounded and raises the error word if it
-// runs out. Producers publish with a fence and an atomic add; consumers read counters with
+// decreasing item size (or, with the shape's interleaved unit order, each item's SELECT and
+// WEIGHTS units placed after the KNN units of items further down, so that both phases share
+// the SMs, and the FINAL units last); CTAs take units in list order from one atomic counter.
+// A unit only waits on units earlier in the list, which running CTAs have already taken and
+// never block on later ones, so the waits end; each wait is still bounded and raises the error
+// word if it runs out. Producers publish with a fence and an atomic add; consumers read counters with
 // acquire loads and results with L2 loads.
 #include <algorithm>
 #include <cstring>
@@ -386,7 +388,7 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         cnt_off[i] = cnt_total;
         cnt_total += sizeof(uint32_t) * (d.knn.qblocks + 1 + d.w.qblocks);
     }
-    // Units: phases in order, items in decreasing size within each phase.
+    // Units: items in decreasing size within each phase; phase by phase, or interleaved.
     std::vector<int32_t> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -394,17 +396,48 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
                static_cast<double>(h[b].m) * h[b].ds.n_pad;
     });
     std::vector<WorkUnit> u;
-    for (int32_t i : order)
+    auto knn_units = [&](int32_t i) {
         for (int qb = 0; qb < h[i].knn.qblocks; ++qb)
             for (int s = 0; s < h[i].knn.splits; ++s)
                 u.push_back({i, qb, s, kUnitKnn});
-    for (int32_t i : order)
+    };
+    auto select_units = [&](int32_t i) {
         for (int qb = 0; qb < h[i].knn.qblocks; ++qb)
             u.push_back({i, qb, 0, kUnitSelect});
-    for (int32_t i : order)
+    };
+    auto weight_units = [&](int32_t i) {
         for (int qb = 0; qb < h[i].w.qblocks; ++qb)
             for (int s = 0; s < h[i].w.splits; ++s)
                 u.push_back({i, qb, s, kUnitWeights});
+    };
+    if (cfg.unit_order == 1) {
+        // Interleaved: phase-1 units run ahead by about two waves of CTAs; each item's SELECT
+        // and WEIGHTS units follow once its phase-1 units are that far back in the list, with
+        // the phase-1 units of the next item after them, so both phases share the SMs.
+        const size_t lead = static_cast<size_t>(2 * 4 * ctx_sm_count(ctx));
+        size_t queued = 0;
+        int32_t next = 0;
+        while (next < count && queued < lead) {
+            queued += static_cast<size_t>(h[order[next]].knn.qblocks) * h[order[next]].knn.splits;
+            knn_units(order[next++]);
+        }
+        for (int32_t ii = 0; ii < count; ++ii) {
+            while (next <= ii)
+                knn_units(order[next++]);
+            select_units(order[ii]);
+            weight_units(order[ii]);
+            if (next < count)
+                knn_units(order[next++]);
+        }
+    } else {
+        for (int32_t i : order)
+            knn_units(i);
+        for (int32_t i : order)
+            select_units(i);
+        for (int32_t i : order)
+            weight_units(i);
+    }
+    // FINAL units last: each waits for its block's WEIGHTS units, all taken long before.
     for (int32_t i : order)
         for (int qb = 0; qb < h[i].w.qblocks; ++qb)
             u.push_back({i, qb, 0, kUnitFinal});

@@ -24,6 +24,7 @@ NEUTRAL = [
     dict(knn_queries_per_thread=2),
     dict(queries_per_thread=8, tile_points=256, knn_list=32, ctas_per_sm=2),
     dict(queries_per_thread=2, knn_queries_per_thread=2, knn_list=16),
+    dict(unit_order=1),
 ]
 
 

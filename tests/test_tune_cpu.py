@@ -26,7 +26,7 @@ def test_default_shape_and_layout():
     c = aidw.tune_config()
     assert c.as_dict() == {"queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
                            "split_points": 65536, "ctas_per_sm": 0,
-                           "knn_queries_per_thread": 0}
+                           "knn_queries_per_thread": 0, "unit_order": 0}
     assert aidw.tune_config_valid(c)
 
 
@@ -37,6 +37,7 @@ def test_default_shape_and_layout():
     ("split_points", [2048, 16384, 65536, 4194304]),
     ("ctas_per_sm", [0, 1, 3, 32]),
     ("knn_queries_per_thread", [0, 2, 4]),
+    ("unit_order", [0, 1]),
 ])
 def test_accepted_values(field, values):
     for v in values:
@@ -51,6 +52,7 @@ def test_accepted_values(field, values):
     ("split_points", 8388608),
     ("ctas_per_sm", -1), ("ctas_per_sm", 33),
     ("knn_queries_per_thread", 1), ("knn_queries_per_thread", 8),
+    ("unit_order", 2), ("unit_order", -1),
 ])
 def test_rejected_values(field, value):
     assert not aidw.tune_config_valid(aidw.tune_config(**{field: value}))
@@ -58,7 +60,7 @@ def test_rejected_values(field, value):
 
 def test_reserved_fields_must_be_zero():
     c = aidw.tune_config()
-    c.reserved[1] = 7
+    c.reserved = 7
     assert not aidw.tune_config_valid(c)
 
 
@@ -111,7 +113,8 @@ def test_save_writes_json_lines_and_load_round_trips(tmp_path):
         "interpolate dev=sm_103 x152 n=2^20 m=2^20 k=10": (aidw.tune_config(), 365.25),
         "batch dev=sm_103 x152 items=256 q=2^22 pairs=2^38 kmax=15":
             (aidw.tune_config(queries_per_thread=8, tile_points=256, knn_list=16,
-                              split_points=131072, ctas_per_sm=3, knn_queries_per_thread=2),
+                              split_points=131072, ctas_per_sm=3, knn_queries_per_thread=2,
+                              unit_order=1),
              88.5),
     }
     for k, (c, ms) in entries.items():
@@ -138,16 +141,17 @@ def test_load_accepts_other_whitespace_and_blank_lines(tmp_path):
     path.write_text(
         "\n"
         '{ "key" : "a b", "queries_per_thread":2,"tile_points" :256, "knn_list": 32 ,'
-        ' "split_points": 16384, "ctas_per_sm": 1, "knn_queries_per_thread" :2, "ms": 1e2 }\n'
+        ' "split_points": 16384, "ctas_per_sm": 1, "knn_queries_per_thread" :2,'
+        ' "unit_order":1, "ms": 1e2 }\n'
         "   \n"
         + json.dumps({"key": "c", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
                       "split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0,
-                      "ms": -1}) + "\n")
+                      "unit_order": 0, "ms": -1}) + "\n")
     assert aidw.TuneCache.load(str(path)) == aidw.OK
     a = aidw.TuneCache.get("a b")
     assert a[0] == aidw.tune_config(queries_per_thread=2, tile_points=256, knn_list=32,
                                     split_points=16384, ctas_per_sm=1,
-                                    knn_queries_per_thread=2)
+                                    knn_queries_per_thread=2, unit_order=1)
     assert a[1] == 100.0
     assert aidw.TuneCache.get("c")[0] == aidw.tune_config()
 
@@ -155,17 +159,19 @@ def test_load_accepts_other_whitespace_and_blank_lines(tmp_path):
 @pytest.mark.parametrize("bad", [
     '{"key": "x", "queries_per_thread": 4}',                     # fields missing
     '{"key": "x", "queries_per_thread": 3, "tile_points": 512, "knn_list": 0, '
-    '"split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "ms": 1}',
+    '"split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "unit_order": 0, '
+    '"ms": 1}',
     '{"key": "x", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0, '
-    '"split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "ms": 1} trailing',
+    '"split_points": 65536, "ctas_per_sm": 0, "knn_queries_per_thread": 0, "unit_order": 0, '
+    '"ms": 1} trailing',
     '{"key": "x", "queries_per_thread": 4, "tile_points": 512, "knn_list": 0, '
-    '"split_points": 65536, "ctas_per_sm": 0, "ms": 1}',         # older layout, field missing
+    '"split_points": 65536, "ctas_per_sm": 0, "ms": 1}',         # older layout, fields missing
     "not json at all",
 ])
 def test_load_rejects_malformed_files_without_merging(tmp_path, bad):
     good = json.dumps({"key": "good", "queries_per_thread": 4, "tile_points": 512,
                        "knn_list": 0, "split_points": 65536, "ctas_per_sm": 0,
-                       "knn_queries_per_thread": 0, "ms": 1.0})
+                       "knn_queries_per_thread": 0, "unit_order": 0, "ms": 1.0})
     path = tmp_path / "bad.jsonl"
     path.write_text(good + "\n" + bad + "\n")
     assert aidw.TuneCache.load(str(path)) == aidw.ERR_INVALID_ARG
