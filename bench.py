@@ -648,10 +648,14 @@ def run_gpu(args):
 
     line = None
     if rank == 0:
-        threads = os.cpu_count() or 1
-        cpu_v, cpu_sample, cpu_threads = oracle_rate(wl, args.cpu_seconds, threads)
-        # The same oracle on one core (the paper's CPU baseline is serial).
-        cpu1_v, cpu1_sample, _ = oracle_rate(wl, args.cpu_seconds / 3.0, 1)
+        # The CPU baseline is timed at N = 1 only (with more ranks the host cores are busy
+        # feeding the other GPUs): the oracle on all host cores, and on one core (the paper's CPU
+        # baseline is serial).
+        cpu_v = cpu1_v = None
+        if world == 1:
+            threads = os.cpu_count() or 1
+            cpu_v, cpu_sample, cpu_threads = oracle_rate(wl, args.cpu_seconds, threads)
+            cpu1_v, cpu1_sample, _ = oracle_rate(wl, args.cpu_seconds / 3.0, 1)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -708,17 +712,20 @@ def run_gpu(args):
             "served": served,
             "gpu_launches": sum(t.launches for t in ktimes),
             "clocks": clk,
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads,
-                             "kind": "oracle", "sample": cpu_sample},
-            "cpu_single_core": {"value": cpu1_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": cpu1_sample},
+            "cpu_baseline": None if cpu_v is None else {
+                "value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                "sample": cpu_sample},
+            "cpu_single_core": None if cpu1_v is None else {
+                "value": cpu1_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": cpu1_sample},
             "paper_context": {"gt730m_tiled_soa_1000K_pair_evals_s": 6.2e9,
                               "speedups_over_serial_cpu": {"fp32_naive": 270, "fp32_tiled": 400,
                                                            "fp64": 8},
-                              "this_build_over_cpu_oracle": {
+                              "this_build_over_cpu_oracle": None if cpu_v is None else {
                                   "fp32": value / cpu_v, "fp64": fp64_rate / cpu_v},
-                              "this_build_over_single_core_oracle": {
-                                  "fp32": value / cpu1_v, "fp64": fp64_rate / cpu1_v},
+                              "this_build_over_single_core_oracle":
+                                  None if cpu1_v is None else {
+                                      "fp32": value / cpu1_v, "fp64": fp64_rate / cpu1_v},
                               "note": "paper: GeForce GT 730M vs one core of an Intel Core "
                                       "i7-4700MQ, N = 1,024,000, transfers included; here: "
                                       "GB300 vs the FP64 oracle on all host cores; different "
