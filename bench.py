@@ -643,7 +643,11 @@ def run_gpu(args):
     served = None
     if world == 1 or rank == 0:
         sctx = aidw.Context(local)
+        # The serving runtime batches many small requests like the batched workload: it runs
+        # with the kernel shape the autotuner picked there.
+        sctx.set_tune_config(aidw.tune_config(**batched["tuned_config"]))
         served = bench_served(sctx, value / world, 2.0, 0.5)
+        served["kernel_shape"] = batched["tuned_config"]
         sctx.close()
 
     line = None
