@@ -44,14 +44,15 @@ LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per 
 
 
 def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
-    kernel's sources changed since the capture (the counters would no longer describe it)."""
+    """DRAM bytes per launch of `kernel` (the template instance the timed step launches) from
+    the committed ncu capture, or None when the capture is of another instance or the kernel's
+    sources changed since (the counters would no longer describe it)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "weights_kernel_traffic_uniform_1Mx1M.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if not rec["kernel"].startswith(kernel):
+        if rec["kernel"] != kernel:
             return None
         for rel, sha in rec["source_sha1"].items():
             with open(os.path.join(ROOT, rel), "rb") as g:
@@ -561,6 +562,7 @@ def run_gpu(args):
     ks = statistics.mean(t.select_ms for t in ktimes)
     kf = statistics.mean(t.finalize_ms for t in ktimes)
     rates = ctx.pipe_rates()
+    shape = ctx.tune_config()
     sm = rates.sm_count
     sm_mhz_peak = 2070.0
     try:
@@ -675,8 +677,10 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "kernel": f"f32_{dominant}_kernel",
                          "achieved": achieved, "peak": peak, "unit": UNIT,
                          "frac": achieved / peak,
-                         "traffic": (measured_traffic("f32_weights_kernel")
-                                     if wl.n == N_DATA and wl.m == M_QUERY else None),
+                         "traffic": (measured_traffic(
+                             f"f32_weights_kernel<{shape.queries_per_thread}, "
+                             f"{shape.tile_points}>") if wl.n == N_DATA and wl.m == M_QUERY
+                             else None),
                          "traffic_unit": "bytes per launch (ncu, committed capture)",
                          "peak_basis": (f"{sm} SMs x {sm_mhz_peak:.0f} MHz (max SM clock) / "
                                         "max(7 FP32 ops / 128 lanes, 1/ex2 + 1/lg2 measured MUFU "

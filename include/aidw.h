@@ -222,9 +222,8 @@ typedef struct aidw_tune_config {
     int32_t reserved;           /* zero */
 } aidw_tune_config;
 
-/* Fills the built-in shape: 4 queries per thread, 512-point tiles, the smallest list, 65,536
- * points per batch work unit, full occupancy, phase-1 queries per thread by list length,
- * phase-by-phase unit order. */
+/* Fills the built-in shape: 2 queries per thread in both phases, 512-point tiles, the smallest
+ * list, 65,536 points per batch work unit, full occupancy, phase-by-phase unit order. */
 int aidw_tune_config_default(aidw_tune_config *out);
 /* AIDW_OK if every field is one of the values above, else AIDW_ERR_INVALID_ARG. */
 int aidw_tune_config_check(const aidw_tune_config *cfg);

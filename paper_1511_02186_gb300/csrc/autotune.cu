@@ -23,12 +23,12 @@ namespace aidw {
 aidw_tune_config tune_default()
 {
     aidw_tune_config c{};
-    c.queries_per_thread = 4;
+    c.queries_per_thread = 2;
     c.tile_points = 512;
     c.knn_list = 0;
     c.split_points = 65536;
     c.ctas_per_sm = 0;
-    c.knn_queries_per_thread = 0;
+    c.knn_queries_per_thread = 2;
     c.unit_order = 0;
     return c;
 }

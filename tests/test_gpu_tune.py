@@ -16,7 +16,8 @@ from parity import TOL_F32, oracle_for, params_of, rel_err, to_device
 pytestmark = pytest.mark.gpu
 
 NEUTRAL = [
-    dict(queries_per_thread=2),
+    dict(queries_per_thread=4, knn_queries_per_thread=0),
+    dict(queries_per_thread=4),
     dict(queries_per_thread=8),
     dict(tile_points=256),
     dict(knn_list=16),

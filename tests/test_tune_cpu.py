@@ -24,9 +24,9 @@ def empty_cache():
 def test_default_shape_and_layout():
     assert ctypes.sizeof(aidw.TuneConfig) == 32
     c = aidw.tune_config()
-    assert c.as_dict() == {"queries_per_thread": 4, "tile_points": 512, "knn_list": 0,
+    assert c.as_dict() == {"queries_per_thread": 2, "tile_points": 512, "knn_list": 0,
                            "split_points": 65536, "ctas_per_sm": 0,
-                           "knn_queries_per_thread": 0, "unit_order": 0}
+                           "knn_queries_per_thread": 2, "unit_order": 0}
     assert aidw.tune_config_valid(c)
 
 
@@ -153,7 +153,8 @@ def test_load_accepts_other_whitespace_and_blank_lines(tmp_path):
                                     split_points=16384, ctas_per_sm=1,
                                     knn_queries_per_thread=2, unit_order=1)
     assert a[1] == 100.0
-    assert aidw.TuneCache.get("c")[0] == aidw.tune_config()
+    assert aidw.TuneCache.get("c")[0] == aidw.tune_config(queries_per_thread=4,
+                                                          knn_queries_per_thread=0)
 
 
 @pytest.mark.parametrize("bad", [
