@@ -167,7 +167,9 @@ int aidw_interpolate_paper(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const
                            int32_t version, int32_t layout, void *stream);
 
 /* ---- batched launch (many datasets in one persistent kernel) -------------------------- */
-/* One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays of the context's
+/* The paper interpolates one dataset per launch; batching independent problems (Sec. 3.1.1:
+ * every query is independent, so every item is too) is this library's addition.
+ * One entry of a batch: a dataset, its queries and outputs (all DEVICE arrays of the context's
  * device, float) and its parameters (precision must be AIDW_F32C; k and levels may differ per
  * item). The kNN index output is not available in batches. */
 typedef struct aidw_batch_item {
@@ -282,7 +284,8 @@ int aidw_tune_cache_save(const char *path);
 int aidw_tune_cache_load(const char *path);
 
 /* ---- serving: asynchronous requests with continuous batching --------------------------- */
-/* Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host
+/* Serving has no counterpart in the paper; each request is one interpolation as above.
+ * Enqueues one interpolation request (same arguments as aidw_interpolate; arrays may be host
  * or device and must stay valid until aidw_poll/aidw_wait report completion). The context's
  * serving thread, started on first use, admits queued requests in arrival order while their
  * device footprint fits the serving budget and packs them into persistent batch launches
@@ -330,7 +333,8 @@ typedef struct aidw_serving_stats {
 
 int aidw_serving_get_stats(aidw_ctx *ctx, aidw_serving_stats *out);
 
-/* ---- diagnostics ---------------------------------------------------------------------- */
+/* ---- diagnostics (the library's own; no counterpart in the paper) ------------------------ */
+/* Names a status code ("unknown status" for any other value); the string is static. */
 const char *aidw_status_string(int status);
 
 /* Checks the context's on-device error word (set by a bounded wait inside a kernel that ran
