@@ -43,21 +43,31 @@ FP64_PIPE_PER_CLK_SM = 2.0  # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 DFMA per
 LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
 
 
+def source_digest(path: str) -> str:
+    """SHA-1 of a C++ source with comments and whitespace removed: edits to comments alone do
+    not change it, any change to the code does."""
+    import hashlib
+    import re
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha1(" ".join(text.split()).encode()).hexdigest()
+
+
 def measured_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` (the template instance the timed step launches) from
-    the committed ncu capture, or None when the capture is of another instance or the kernel's
-    sources changed since (the counters would no longer describe it)."""
-    import hashlib
+    the committed ncu capture, or None when the capture is of another instance or the code of
+    the kernel's sources changed since (the counters would no longer describe it)."""
     path = os.path.join(ROOT, "profiles", "weights_kernel_traffic_uniform_1Mx1M.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec["kernel"] != kernel:
             return None
-        for rel, sha in rec["source_sha1"].items():
-            with open(os.path.join(ROOT, rel), "rb") as g:
-                if hashlib.sha1(g.read()).hexdigest() != sha:
-                    return None
+        for rel, digest in rec["source_digest"].items():
+            if source_digest(os.path.join(ROOT, rel)) != digest:
+                return None
         return rec["dram_read_bytes"] + rec["dram_write_bytes"]
     except (OSError, KeyError, ValueError):
         return None

@@ -5,7 +5,7 @@
 // the batch), so an item's result is bit-identical whether it runs alone or in any mix:
 //   KNN     (item, query block)         pruned phase-1 scan of Z-ordered      (no wait)
 //                                       queries (nearest data tiles first)
-//   SELECT  (item, query block)         merge + Eq. 2-6 for 512 queries      waits for the
+//   SELECT  (item, query block)         merge + Eq. 2-6 for the block        waits for the
 //                                                                            block's KNN splits
 //   WEIGHTS (item, query block, split)  phase-2 scan of one data split       waits for all of
 //                                                                            the item's SELECTs

@@ -279,11 +279,15 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
 // ---------------------------------------------------------------------------------------------
 // Phase 1 over Z-ordered queries, one CTA per query block and no data splits. The CTA takes the
 // bounding box of its queries, computes for every data tile a lower bound of the squared
-// distance between the two boxes, sorts the tiles by it (bitonic sort in shared memory) and
-// visits them nearest first. After each tile it takes T = the largest k-th squared distance of
-// its queries; it stops at the first tile whose bound exceeds T. No skipped point could enter a
-// list: its exact FP32 distance is at least the box bound (the bound is shrunk by 2^-20 to
-// cover rounding), which exceeds every query's current k-th distance.
+// distance between the two boxes, sorts the tiles by it and, among equal bounds, by the distance
+// between the box centres (bitonic sort in shared memory), and visits them in that order. After
+// each tile it takes T = the largest k-th squared distance of its queries; it stops at the first
+// tile whose bound exceeds T. Each warp (32 Q consecutive queries) also skips a tile whose bound
+// to the warp's own box exceeds the warp's largest k-th distance, and, inside a tile, every
+// 64-point sub-tile whose bound exceeds the k-th distance of each of its queries (knn_tile). No
+// skipped point could enter a list: its exact FP32 distance is at least the box bound (the
+// bound is shrunk by 2^-20 to cover rounding), which exceeds every affected query's current
+// k-th distance.
 // ---------------------------------------------------------------------------------------------
 
 // Shared-memory scratch of a pruned phase-1 unit.
