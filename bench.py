@@ -658,7 +658,7 @@ def run_gpu(args):
         # The serving runtime batches many small requests like the batched workload: it runs
         # with the kernel shape the autotuner picked there.
         sctx.set_tune_config(aidw.tune_config(**batched["tuned_config"]))
-        served = bench_served(sctx, value / world, 2.0, 0.5)
+        served = bench_served(sctx, value / world, 2.0, args.nominal_window)
         served["kernel_shape"] = batched["tuned_config"]
         sctx.close()
 
@@ -769,6 +769,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=N_DATA,
                     help="data and query count (smaller sizes only for profiling runs)")
+    ap.add_argument("--nominal-window", type=float, default=0.5,
+                    help="arrival window (s) of the served run at the nominal 2,000 req/s; its "
+                         "offered load is several times the capacity, so the run lasts about "
+                         "8 s per second of window")
     ap.add_argument("--m", type=int, default=0,
                     help="query count (default: --n; smaller sizes only for profiling runs)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
