@@ -413,9 +413,8 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
 // more than it saves).
 constexpr int64_t kCullMinQueries = 2048;
 
-// The pruned phase 1 serves FP32 calls, and FP64 calls that do not ask for the neighbour
-// indices (the FP64 index lists keep the oracle's tie order, which needs the caller-order scan),
-// when there are enough queries: with m queries spread over the data, a block of q queries
+// The pruned phase 1 serves both precisions (FP64 lists with indices keep the oracle's tie order
+// by ordering pairs (distance, caller index)) when there are enough queries: with m queries spread over the data, a block of q queries
 // covers about q/m of the area, so each of the m/q blocks visits about n q / (512 m) tiles, and
 // with fewer blocks than the GPU holds (P) the pruned scan takes about n q^2 P / m per-pair
 // steps of one CTA against n m / P steps of each CTA for the split scan: the pruned scan wins
@@ -425,8 +424,10 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
                     const Plan &pl)
 {
     const double need = kThreads * pl.kq * std::sqrt(static_cast<double>(pl.knn_slots));
+    (void)precision;
+    (void)with_idx;
     return ds.n_pad / kTileF32Knn <= kMaxCullTiles && m >= kCullMinQueries &&
-           static_cast<double>(m) >= need && (precision == AIDW_F32C || !with_idx);
+           static_cast<double>(m) >= need;
 }
 
 size_t culled_extra_bytes(int64_t m, int precision)

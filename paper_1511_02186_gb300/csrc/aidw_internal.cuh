@@ -151,9 +151,10 @@ cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *q
 cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
                               cudaStream_t st, const uint32_t *perm = nullptr);
-// Phase 1 over Z-ordered FP64 queries, pruned like launch_f32_knn_cull, distances only (the
-// neighbour distances, not which of tied points, decide r_obs); sqx / sqy are the queries in
-// Z-order and the dataset's points are read through its Z-order map.
+// Phase 1 over Z-ordered FP64 queries, pruned like launch_f32_knn_cull; with pl.with_idx the
+// lists are the k smallest (distance, caller index) pairs, so ties go to the lower index as in
+// the caller-order scan; sqx / sqy are the queries in Z-order and the dataset's points are read
+// through its Z-order map.
 cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const double *sqx,
                                 const double *sqy, int k, const Scratch &sc, int *err,
                                 cudaStream_t st);

@@ -186,8 +186,10 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
 // Phase 1 over Z-ordered FP64 queries, pruned as the FP32 path's (one CTA per query block, data
 // tiles visited in order of a lower bound of the box-to-box distance, nearest centre first among
 // equal bounds, the block stopping at the first tile beyond its queries' largest k-th distance,
-// each warp skipping tiles beyond its own), keeping distances only: the k nearest distances, and
-// so r_obs, do not depend on which of two tied points is kept. A tile's points are gathered from
+// each warp skipping tiles beyond its own). Without the kNN output it keeps distances only (the
+// k nearest distances, and so r_obs, do not depend on which of two tied points is kept); with
+// it, it keeps the k smallest pairs (distance, caller index), i.e. ties to the lower index as
+// the caller-order scan with strict "<" has them. A tile's points are gathered from
 // the caller-order FP64 copy through the Z-order map. The tile boxes hold the FP32 coordinates;
 // widened by 2^-23 of their largest magnitude they contain the FP64 points (FP32 rounding moves a
 // coordinate by at most 2^-24 of it), and the bound is shrunk by 2^-50 to cover its own rounding
@@ -204,14 +206,33 @@ __device__ __forceinline__ double box_bound64(float4 tb, double qx0, double qy0,
     return (dx * dx + dy * dy) * (1.0 - 0x1p-50);
 }
 
-template <int KP, int Q>
+// Lexicographic insertion of (v, vi) into the ascending (distance, index) register lists of one
+// query: the k smallest pairs, so that ties go to the lower caller index as in the scan order.
+template <int KP>
+__device__ __forceinline__ void pair_insert(double (&L)[KP], int32_t (&I)[KP], double v,
+                                            int32_t vi)
+{
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        const bool lt = v < L[j] || (v == L[j] && vi < I[j]);
+        const double lo = lt ? v : L[j];
+        const int32_t loi = lt ? vi : I[j];
+        v = lt ? L[j] : v;
+        vi = lt ? I[j] : vi;
+        L[j] = lo;
+        I[j] = loi;
+    }
+}
+
+template <int KP, int Q, bool IDX>
 __global__ void __launch_bounds__(kThreads)
 f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2,
                     const double *__restrict__ sqx, const double *__restrict__ sqy, int k,
-                    double *__restrict__ part_d2)
+                    double *__restrict__ part_d2, int32_t *__restrict__ part_idx)
 {
     extern __shared__ unsigned long long order[];  // [ntiles_p2] sort keys
     __shared__ __align__(16) double2 tile[kTileF32Knn];
+    __shared__ int32_t tidx[IDX ? kTileF32Knn : 1];  // caller index of each tile point
     constexpr int W = kThreads / 32;
     __shared__ double red[4][W];
     __shared__ double sbox[4];
@@ -222,6 +243,7 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
 
     double qxr[Q], qyr[Q];
     double L[Q][KP];
+    int32_t I[Q][IDX ? KP : 1];
     double bx0 = CUDART_INF, by0 = CUDART_INF, bx1 = -CUDART_INF, by1 = -CUDART_INF;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -233,8 +255,11 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
         bx1 = fmax(bx1, qxr[j]);
         by1 = fmax(by1, qyr[j]);
 #pragma unroll
-        for (int i = 0; i < KP; ++i)
+        for (int i = 0; i < KP; ++i) {
             L[j][i] = (i < KP - k) ? -CUDART_INF : CUDART_INF;
+            if constexpr (IDX)
+                I[j][i] = (i < KP - k) ? -1 : INT32_MAX;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         bx0 = fmin(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
@@ -309,10 +334,12 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
         for (int u = tid; u < kTileF32Knn; u += kThreads) {
             const int32_t o = ds.orig[t * kTileF32Knn + u];
             tile[u] = o >= 0 ? ds.xy64[o] : make_double2(CUDART_INF, CUDART_INF);
+            if (IDX)
+                tidx[u] = o;
         }
         __syncthreads();
         const double wlb = box_bound64(ds.tile_box[t], wx0, wy0, wx1, wy1);
-        if (!(wlb > wthr)) {
+        if (!(wlb > wthr)) {  // a tie needs d == wthr, and the bound is strictly below d
             for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
                 double mn[Q];
 #pragma unroll
@@ -327,13 +354,20 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
                 }
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
-                    if (mn[j] < L[j][KP - 1]) {
+                    // With indices a tie with the k-th distance may still enter (lower index).
+                    if (IDX ? mn[j] <= L[j][KP - 1] : mn[j] < L[j][KP - 1]) {
 #pragma unroll 1
                         for (int u = 0; u < kChunkKnn; ++u) {
                             const double2 p = tile[c + u];
                             const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
-                            if (d < L[j][KP - 1])
+                            if constexpr (IDX) {
+                                const int32_t id = tidx[c + u];
+                                if (d < L[j][KP - 1] ||
+                                    (d == L[j][KP - 1] && id < I[j][KP - 1]))
+                                    pair_insert<KP>(L[j], I[j], d, id);
+                            } else if (d < L[j][KP - 1]) {
                                 list_insert<KP>(L[j], d);
+                            }
                         }
                     }
                 }
@@ -365,8 +399,11 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
 #pragma unroll
         for (int i = 0; i < KP; ++i) {
             const int r = i - (KP - k);
-            if (r >= 0)
+            if (r >= 0) {
                 part_d2[static_cast<int64_t>(r) * m + q] = L[j][i];
+                if constexpr (IDX)
+                    part_idx[static_cast<int64_t>(r) * m + q] = I[j][i];
+            }
         }
     }
 }
@@ -399,7 +436,7 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
             d1 = hd[bs];
         r_sum = __dadd_rn(r_sum, __dsqrt_rn(hd[bs]));  // Eq. 3, ascending order
         if (out_knn)
-            out_knn[q * k + r] = hi[bs];
+            out_knn[(perm ? static_cast<int64_t>(perm[q]) : q) * k + r] = hi[bs];
         if (++cur[bs] < k) {
             const int64_t o = (static_cast<int64_t>(bs) * k + cur[bs]) * m + q;
             hd[bs] = part_d2[o];
@@ -648,7 +685,7 @@ cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMa
     return cudaGetLastError();
 }
 
-template <int KP>
+template <int KP, bool IDX>
 cudaError_t launch_cull64_t(const DatasetDev &ds, const Plan &pl, const double *sqx,
                             const double *sqy, int k, const Scratch &sc, cudaStream_t st)
 {
@@ -658,13 +695,14 @@ cudaError_t launch_cull64_t(const DatasetDev &ds, const Plan &pl, const double *
     while (p2 < ntiles)
         p2 <<= 1;
     const size_t dyn = sizeof(unsigned long long) * p2;
-    auto fn = f64_knn_cull_kernel<KP, Q>;
+    auto fn = f64_knn_cull_kernel<KP, Q, IDX>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(dyn));
     if (e != cudaSuccess)
         return e;
     fn<<<pl.knn.qblocks, kThreads, dyn, st>>>(ds, pl.m, pl.knn.q_per_block, ntiles, p2, sqx,
-                                              sqy, k, static_cast<double *>(sc.part_d2));
+                                              sqy, k, static_cast<double *>(sc.part_d2),
+                                              sc.part_idx);
     return cudaGetLastError();
 }
 
@@ -673,11 +711,15 @@ cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const doub
                                 cudaStream_t st)
 {
     (void)err;  // no bounded waits: tiles are gathered with plain loads
+    const bool idx = pl.with_idx;
     if (k <= 8)
-        return launch_cull64_t<8>(ds, pl, sqx, sqy, k, sc, st);
+        return idx ? launch_cull64_t<8, true>(ds, pl, sqx, sqy, k, sc, st)
+                   : launch_cull64_t<8, false>(ds, pl, sqx, sqy, k, sc, st);
     if (k <= 16)
-        return launch_cull64_t<16>(ds, pl, sqx, sqy, k, sc, st);
-    return launch_cull64_t<32>(ds, pl, sqx, sqy, k, sc, st);
+        return idx ? launch_cull64_t<16, true>(ds, pl, sqx, sqy, k, sc, st)
+                   : launch_cull64_t<16, false>(ds, pl, sqx, sqy, k, sc, st);
+    return idx ? launch_cull64_t<32, true>(ds, pl, sqx, sqy, k, sc, st)
+               : launch_cull64_t<32, false>(ds, pl, sqx, sqy, k, sc, st);
 }
 
 cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,

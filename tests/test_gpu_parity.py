@@ -265,9 +265,10 @@ def _fp64_cases():
 @pytest.mark.parametrize("idx", range(5), ids=["uniform", "clustered_k17", "clustered_k32",
                                                "lattice_ties", "large_offset"])
 def test_fp64_pruned_knn_equals_caller_order_scan(ctx, idx):
-    """FP64 calls without the kNN output take the pruned phase 1 over Z-ordered queries; with it,
-    the caller-order scan. Both give the same neighbour distances, hence bit-identical alpha and
-    Z, and both match the oracle at 1e-12."""
+    """FP64 with enough queries takes the pruned phase 1 over Z-ordered queries, with or without
+    the kNN output (then the lists hold the k smallest (distance, caller index) pairs); forced
+    splits take the caller-order scan. All give bit-identical alpha and Z and the oracle's kNN
+    lists bit for bit (ties to the lower index), and Z within 1e-12 of the oracle."""
     import torch
     wl = _fp64_cases()[idx]
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
@@ -276,15 +277,18 @@ def test_fp64_pruned_knn_equals_caller_order_scan(ctx, idx):
     ctx.set_profiling(True)
     z1, a1, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True)
     assert ctx.kernel_times().launches == 18  # ordering + pruned phase 1
-    z2, a2, kn = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    z2, a2, kn2 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    assert ctx.kernel_times().launches == 18
+    z3, a3, kn3 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True, splits=(4, 0))
     assert ctx.kernel_times().launches == 4   # caller-order scan
     ctx.set_profiling(False)
     torch.cuda.synchronize()
-    assert torch.equal(a1, a2)
-    assert torch.equal(z1, z2)
+    assert torch.equal(a1, a2) and torch.equal(a1, a3)
+    assert torch.equal(z1, z2) and torch.equal(z1, z3)
     ref, src = oracle_for(wl, aidw.F64)
     assert rel_err(z1.cpu().numpy(), ref).max() <= TOL_F64
-    assert np.array_equal(kn.cpu().numpy(), ref["knn"])
+    assert np.array_equal(kn2.cpu().numpy(), ref["knn"])
+    assert np.array_equal(kn3.cpu().numpy(), ref["knn"])
     ds.destroy()
 
 
