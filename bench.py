@@ -39,6 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # by phase 2.
 FP32_OPS_P2, MUFU_OPS_P2 = 7, 2
 FP64_OPS_P2 = 31  # FP64 instructions per pair in the FP64 phase-2 kernel
+FP64X_OPS_P2 = 4  # FP64 instructions per pair in the AIDW_F64X phase-2 kernel (the distance)
 FP64_PIPE_PER_CLK_SM = 2.0  # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 DFMA per clk per SM
 LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
 
@@ -522,14 +523,17 @@ def run_gpu(args):
     wl = workloads.uniform_paper(0, n=args.n, m=args.m or args.n)
     ctx = aidw.Context(local)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
-    f64 = args.precision == "f64"
+    f64 = args.precision in ("f64", "f64x")
     if f64 and args.extras:
-        raise SystemExit("--precision f64 is a profiling option: use it with --no-extras")
+        raise SystemExit(f"--precision {args.precision} is a profiling option: use it with "
+                         "--no-extras")
     qdt = torch.float64 if f64 else torch.float32
     qx = torch.as_tensor(wl.qx, dtype=qdt, device=dev)
     qy = torch.as_tensor(wl.qy, dtype=qdt, device=dev)
     out = torch.empty(wl.m, dtype=qdt, device=dev)
-    p = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64 if f64 else aidw.F32C)
+    p = aidw.default_params(k=wl.k, levels=wl.levels,
+                            precision={"f32": aidw.F32C, "f64": aidw.F64,
+                                       "f64x": aidw.F64X}[args.precision])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -599,7 +603,8 @@ def run_gpu(args):
         ds.destroy()
         ctx.close()
         if rank == 0:
-            metric = METRIC if not f64 else "AIDW pair-evals/s (FP64 path)"
+            metric = {"f32": METRIC, "f64": "AIDW pair-evals/s (FP64 path)",
+                      "f64x": "AIDW pair-evals/s (FP64X path)"}[args.precision]
             print(json.dumps({"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup,
                               "config": workload_config(wl), "precision": args.precision,
@@ -629,6 +634,25 @@ def run_gpu(args):
     # GB300's nominal FP64 rate (1.25 TFLOP/s) and the pipe's peak that ncu reports.
     fp64_w_achieved = q64 * wl.n / (kt64.weights_ms / 1e3)
     fp64_w_peak = sm * clk_hz * FP64_PIPE_PER_CLK_SM / FP64_OPS_P2
+
+    # AIDW_F64X (FP64 phase 1 and alpha, double-float phase 2) on a larger query sample, timed
+    # the same way; its phase 2 is bound by the four FP64 instructions of each pair's distance.
+    q64x = 131072
+    idx_x = torch.as_tensor(np.random.default_rng(10).choice(wl.m, q64x, replace=False))
+    qx64x = torch.as_tensor(wl.qx, dtype=torch.float64, device=dev)[idx_x.to(dev)].contiguous()
+    qy64x = torch.as_tensor(wl.qy, dtype=torch.float64, device=dev)[idx_x.to(dev)].contiguous()
+    p64x = aidw.default_params(k=wl.k, levels=wl.levels, precision=aidw.F64X)
+    ctx.interpolate(ds, qx64x, qy64x, p64x, stream=stream.cuda_stream)
+    ctx.set_profiling(True)
+    e0.record(stream)
+    ctx.interpolate(ds, qx64x, qy64x, p64x, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kt64x = ctx.kernel_times()
+    ctx.set_profiling(False)
+    fp64x_rate = q64x * wl.n / (e0.elapsed_time(e1) / 1e3)
+    fp64x_w_achieved = q64x * wl.n / (kt64x.weights_ms / 1e3)
+    fp64x_w_peak = sm * clk_hz * FP64_PIPE_PER_CLK_SM / FP64X_OPS_P2
 
     # End to end through the public API with host buffers: dataset upload (FP64 host arrays),
     # query upload from pinned memory, interpolation, result download.
@@ -721,6 +745,23 @@ def run_gpu(args):
                                                       "1.25 TFLOP/s; ncu's FP64 pipe peak) / "
                                                       f"{FP64_OPS_P2} FP64 instructions per "
                                                       "pair")}},
+            "fp64x_path": {"value": fp64x_rate, "unit": UNIT,
+                           "sample": f"{q64x} seeded queries x all {wl.n} data points",
+                           "kernel_ms": {"knn_incl_query_ordering": kt64x.knn_ms,
+                                         "select": kt64x.select_ms,
+                                         "weights": kt64x.weights_ms,
+                                         "finalize": kt64x.finalize_ms},
+                           "roofline": {"bound": "fp64", "kernel": "f64x_weights_kernel",
+                                        "achieved": fp64x_w_achieved, "peak": fp64x_w_peak,
+                                        "unit": UNIT, "frac": fp64x_w_achieved / fp64x_w_peak,
+                                        "peak_basis": (f"{sm} SMs x {sm_mhz_peak:.0f} MHz x "
+                                                       f"{FP64_PIPE_PER_CLK_SM:g} FP64 "
+                                                       "instructions per clk per SM / "
+                                                       f"{FP64X_OPS_P2} FP64 instructions "
+                                                       "per pair (the squared distance; "
+                                                       "log2, the power, exp2 and the sums "
+                                                       "run in double-float on the FP32 "
+                                                       "pipes)")}},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "includes": "dataset upload + conversion, query upload, both phases, "
@@ -741,7 +782,8 @@ def run_gpu(args):
                               "speedups_over_serial_cpu": {"fp32_naive": 270, "fp32_tiled": 400,
                                                            "fp64": 8},
                               "this_build_over_cpu_oracle": None if cpu_v is None else {
-                                  "fp32": value / cpu_v, "fp64": fp64_rate / cpu_v},
+                                  "fp32": value / cpu_v, "fp64": fp64_rate / cpu_v,
+                                  "fp64x": fp64x_rate / cpu_v},
                               "this_build_over_single_core_oracle":
                                   None if cpu1_v is None else {
                                       "fp32": value / cpu1_v, "fp64": fp64_rate / cpu1_v},
@@ -775,8 +817,9 @@ def main():
                          "8 s per second of window")
     ap.add_argument("--m", type=int, default=0,
                     help="query count (default: --n; smaller sizes only for profiling runs)")
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
-                    help="path of the timed step (f64 only with --no-extras, for profiling)")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f64x"],
+                    help="path of the timed step (f64 and f64x only with --no-extras, for "
+                         "profiling)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the FP64, end-to-end and CPU-baseline measurements")
     args = ap.parse_args()

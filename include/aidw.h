@@ -49,9 +49,17 @@ extern "C" {
 /* AIDW_F32C: distances, kNN selection and weights in FP32; the two weighted sums in FP32 with
  * Kahan-compensated merges; alpha mapping (Eq. 2, 4, 5, 6) and the final ratio in FP64.
  * Queries and the output are float arrays.
- * AIDW_F64: every step in FP64; queries and the output are double arrays. */
+ * AIDW_F64: every step in FP64; queries and the output are double arrays.
+ * AIDW_F64X (the library's addition; the paper has FP32 and FP64 only): FP64 arrays and the
+ * FP64 path's phase 1, neighbour lists and alpha; in phase 2 each pair's squared distance is
+ * formed in FP64 and the rest of its work (log2, the power of Eq. 1, both weighted sums) runs
+ * in double-float arithmetic (pairs of floats, about 48 bits) on the FP32 pipes, which on
+ * GB300 run at about 90 times the FP64 rate. Results agree with the FP64 path to about 1e-13
+ * relative to max(|Z|, sum w|z| / sum w); weights below 2^-126 of the nearest point's are
+ * dropped. */
 #define AIDW_F32C 0
 #define AIDW_F64 1
+#define AIDW_F64X 2
 
 #define AIDW_DTYPE_F32 0
 #define AIDW_DTYPE_F64 1
@@ -66,7 +74,7 @@ typedef int64_t aidw_request;
 /* Parameters of one interpolation (Sec. 2.2). */
 typedef struct aidw_params {
     int32_t k;         /* neighbours for r_obs (Eq. 3); 1 <= k <= min(n, AIDW_MAX_K) */
-    int32_t precision; /* AIDW_F32C or AIDW_F64 */
+    int32_t precision; /* AIDW_F32C, AIDW_F64 or AIDW_F64X */
     double alpha[5];   /* the five levels alpha_1..alpha_5 of Eq. 6; finite, > 0 */
     double r_min;      /* R_min of Eq. 5 (the paper suggests 0.0) */
     double r_max;      /* R_max of Eq. 5 (the paper suggests 2.0); r_max > r_min, r_max > 0 */
@@ -107,8 +115,8 @@ int aidw_dataset_info(aidw_ctx *ctx, aidw_dataset ds, int64_t *n, size_t *device
 
 /* ---- interpolation -------------------------------------------------------------------- */
 /* AIDW at m query points (qx[j], qy[j]) against dataset ds.
- *   qx, qy   m coordinates, float for AIDW_F32C, double for AIDW_F64
- *   out      m predictions Z (Eq. 1), float for AIDW_F32C, double for AIDW_F64
+ *   qx, qy   m coordinates, float for AIDW_F32C, double for AIDW_F64 and AIDW_F64X
+ *   out      m predictions Z (Eq. 1), float for AIDW_F32C, double for AIDW_F64 and AIDW_F64X
  *   out_alpha  nullable; m adaptive powers alpha (Eq. 6) as float
  *   out_knn  nullable; m*k int32 data-point indices, row j holding query j's neighbours in
  *            ascending distance, ties to the lower index (Sec. 3.1.2 with strict "<")
@@ -153,7 +161,7 @@ int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, co
  * (blocks of 256 data points staged in shared memory for the thread block, Sec. 3.1.1), and the
  * data in layout AIDW_LAYOUT_SOA (x[], y[], z[]) or AIDW_LAYOUT_AOAS ({x, y, z, 0} aligned
  * structures, Sec. 3.1.3), copied from the dataset in the caller's order for the call. Precision
- * as p->precision (float or double arrays). Per pair the FP32 arithmetic is aidw_interpolate's;
+ * as p->precision (AIDW_F32C or AIDW_F64: float or double arrays). Per pair the FP32 arithmetic is aidw_interpolate's;
  * in FP64 the weights use the CUDA library's log2 / exp2 (aidw_interpolate's FP64 path has its
  * own table-driven pair). The four variants of one precision give identical results. Device
  * arrays only; stream-ordered.
@@ -384,6 +392,18 @@ int aidw_debug_fail_alloc_after(aidw_ctx *ctx, int64_t after);
  * the next aidw_check_device_errors (or synchronous call) returns AIDW_ERR_TIMEOUT and the
  * context stays usable. Synchronous; returns AIDW_OK once the kernel has finished. */
 int aidw_debug_expire_wait(aidw_ctx *ctx, int32_t which, uint32_t polls);
+
+/* Test hooks for the phase-2 arithmetic, evaluated on the current device (synchronous; DEVICE
+ * arrays of n doubles; INVALID_ARG for n < 0 or a null array, CUDA on a launch error).
+ * aidw_debug_f64_log2_exp2: lx[i] = log2(x[i]) and ey[i] = 2^y[i] by the AIDW_F64 scan's
+ *   table-driven FP64 functions (x positive or +inf).
+ * aidw_debug_df_weight: the AIDW_F64X scan's double-float weight of one pair: v[i] =
+ *   log2(d2[i] / d1sq[i]) and w[i] = 2^(-kappa[i] v[i]), each returned as hi + lo rounded to
+ *   double (d2 and d1sq positive normal, kappa > 0). */
+int aidw_debug_f64_log2_exp2(const double *x, const double *y, int64_t n, double *lx,
+                             double *ey);
+int aidw_debug_df_weight(const double *d2, const double *d1sq, const double *kappa, int64_t n,
+                         double *v, double *w);
 
 #ifdef __cplusplus
 }

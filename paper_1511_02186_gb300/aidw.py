@@ -28,6 +28,7 @@ ERR_UNSUPPORTED = -7
 
 F32C = 0
 F64 = 1
+F64X = 2
 DTYPE_F32 = 0
 DTYPE_F64 = 1
 MAX_K = 32
@@ -157,12 +158,13 @@ SIGNATURES = {
     "aidw_tune_cache_size": (ctypes.c_int, []),
     "aidw_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
     "aidw_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "aidw_debug_f64_log2_exp2": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "aidw_debug_df_weight": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P]),
 }
 # Test-only hooks exported by the library but not declared in the public header.
 DEBUG_SIGNATURES = {
     "aidw_debug_interpolate_splits": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P,
                                                      _I32, _I32]),
-    "aidw_debug_f64_log2_exp2": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
 }
 
 
@@ -394,7 +396,7 @@ class Context:
                     stream=None, splits=None):
         """AIDW at the queries; returns (out, out_alpha or None, out_knn or None)."""
         p = params or default_params()
-        fdt = "f8" if p.precision == F64 else "f4"
+        fdt = "f8" if p.precision in (F64, F64X) else "f4"
         kqx, pqx = _prep(qx, fdt)
         kqy, pqy = _prep(qy, fdt)
         m = int(kqx.shape[0])
@@ -427,7 +429,7 @@ class Context:
         """AIDW by the paper's naive / tiled kernel design with SoA / AoaS data (CUDA
         tensors); returns (out, out_alpha or None)."""
         p = params or default_params()
-        fdt = "f8" if p.precision == F64 else "f4"
+        fdt = "f8" if p.precision in (F64, F64X) else "f4"
         kqx, pqx = _prep(qx, fdt)
         kqy, pqy = _prep(qy, fdt)
         m = int(kqx.shape[0])
@@ -445,7 +447,7 @@ class Context:
 
     def idw(self, ds: Dataset, qx, qy, alpha: float, precision: int = F32C, out=None,
             stream=None):
-        fdt = "f8" if precision == F64 else "f4"
+        fdt = "f8" if precision in (F64, F64X) else "f4"
         kqx, pqx = _prep(qx, fdt)
         kqy, pqy = _prep(qy, fdt)
         m = int(kqx.shape[0])
@@ -515,7 +517,7 @@ class Context:
         """Queue a request; returns (status, request id). The query arrays are kept alive by
         the context until the request is released; output arrays must already have the right
         dtype and be contiguous (they are written in place when the request completes)."""
-        fdt = "f8" if params.precision == F64 else "f4"
+        fdt = "f8" if params.precision in (F64, F64X) else "f4"
         kqx, pqx = _prep(qx, fdt)
         kqy, pqy = _prep(qy, fdt)
         po = _prep_out(out, fdt)

@@ -112,8 +112,8 @@ struct aidw_ctx {
     cudaEvent_t ev[5] = {};
     aidw_kernel_times last{};
     bool last_valid = false;
-    int slots_cache[2][4][2] = {};  // [precision][kp bucket][with_idx] knn slots
-    int wslots_cache[2][3][2] = {};  // [precision][queries per thread 2/4/8][tile 256/512]
+    int slots_cache[3][4][2] = {};  // [precision][kp bucket][with_idx] knn slots
+    int wslots_cache[3][3][2] = {};  // [precision][queries per thread 2/4/8][tile 256/512]
     aidw_tune_config tune = aidw::tune_default();
     ServingRuntime *serving = nullptr;
 };
@@ -243,6 +243,12 @@ static PassPlan plan_pass(int64_t m, int64_t n_pad, int qpb, int slots_total, in
     return pp;
 }
 
+// AIDW_F64 and AIDW_F64X share the FP64 arrays, phase 1, selection and finalisation.
+static bool f64_arrays(int precision)
+{
+    return precision == AIDW_F64 || precision == AIDW_F64X;
+}
+
 static int kp_bucket(int kp)
 {
     return kp <= 8 ? 0 : (kp <= 12 ? 1 : (kp <= 16 ? 2 : 3));
@@ -252,7 +258,8 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
                int force_knn_splits, int force_w_splits, const aidw_tune_config *cfg)
 {
     const aidw_tune_config &tc = cfg ? *cfg : ctx->tune;
-    const bool f64 = precision == AIDW_F64;
+    const bool f64 = f64_arrays(precision);
+    const bool x = precision == AIDW_F64X;
     Plan pl{};
     pl.m = m;
     pl.with_idx = with_idx;
@@ -266,9 +273,11 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     int &ws = ctx->wslots_cache[precision][pl.qw == 2 ? 0 : (pl.qw == 4 ? 1 : 2)]
                                [pl.tw == 256 ? 0 : 1];
     if (!ws)
-        ws = f64 ? f64_w_slots_per_sm() : f32_w_slots_per_sm(pl.qw, pl.tw);
+        ws = x ? f64x_w_slots_per_sm()
+               : (f64 ? f64_w_slots_per_sm() : f32_w_slots_per_sm(pl.qw, pl.tw));
     const int qk = f64 ? f64_knn_queries_per_block(k) : f32_knn_queries_per_block(pl.kp);
-    const int qw = f64 ? f64_w_queries_per_block() : f32_w_queries_per_block(pl.qw);
+    const int qw = x ? f64x_w_queries_per_block()
+                     : (f64 ? f64_w_queries_per_block() : f32_w_queries_per_block(pl.qw));
     // A split restarts its neighbour lists: about k (1 + ln(n_split / k)) insertions per query,
     // each a rescan of a chunk by a partly idle warp. Measured on GB300 at n = m = 2^20,
     // k = 10, every extra split costs about as much as scanning 100,000 more points.
@@ -304,19 +313,19 @@ void ctx_set_tune(aidw_ctx *ctx, const aidw_tune_config &c)
 
 size_t scratch_bytes(int precision, const Plan &pl, int k)
 {
-    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    const size_t es = f64_arrays(precision) ? sizeof(double) : sizeof(float);
     const size_t m = static_cast<size_t>(pl.m);
     size_t b = align256(pl.knn.splits * static_cast<size_t>(k) * m * es);
     if (pl.with_idx)
         b += align256(pl.knn.splits * static_cast<size_t>(k) * m * sizeof(int32_t));
-    b += align256(m * (precision == AIDW_F64 ? sizeof(QParamF64) : sizeof(QParamF32)));
+    b += align256(m * (f64_arrays(precision) ? sizeof(QParamF64) : sizeof(QParamF32)));
     b += align256(pl.w.splits * 4 * m * es);
     return b;
 }
 
 void scratch_carve(void *base, int precision, const Plan &pl, int k, Scratch *s)
 {
-    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    const size_t es = f64_arrays(precision) ? sizeof(double) : sizeof(float);
     const size_t m = static_cast<size_t>(pl.m);
     char *p = static_cast<char *>(base);
     s->part_d2 = p;
@@ -327,7 +336,7 @@ void scratch_carve(void *base, int precision, const Plan &pl, int k, Scratch *s)
         p += align256(pl.knn.splits * static_cast<size_t>(k) * m * sizeof(int32_t));
     }
     s->qparam = p;
-    p += align256(m * (precision == AIDW_F64 ? sizeof(QParamF64) : sizeof(QParamF32)));
+    p += align256(m * (f64_arrays(precision) ? sizeof(QParamF64) : sizeof(QParamF32)));
     s->part_sum = p;
 }
 
@@ -335,7 +344,7 @@ int validate_params(const aidw_params *p, int64_t n)
 {
     if (!p)
         return AIDW_ERR_INVALID_ARG;
-    if (p->precision != AIDW_F32C && p->precision != AIDW_F64)
+    if (p->precision != AIDW_F32C && !f64_arrays(p->precision))
         return AIDW_ERR_INVALID_ARG;
     if (p->k < 1 || p->k > AIDW_MAX_K || p->k > n)
         return AIDW_ERR_INVALID_ARG;
@@ -368,7 +377,8 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
 {
     const AlphaMap am = alpha_map(p);
     cudaError_t e;
-    const bool f64 = p.precision == AIDW_F64;
+    const bool f64 = f64_arrays(p.precision);
+    const bool x = p.precision == AIDW_F64X;
     if (profile)
         cudaEventRecord(ctx->ev[0], st);
     e = f64 ? launch_f64_knn(ds, pl, static_cast<const double *>(qx),
@@ -379,15 +389,17 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
         return AIDW_ERR_CUDA;
     if (profile)
         cudaEventRecord(ctx->ev[1], st);
-    e = f64 ? launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st)
+    e = f64 ? launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, nullptr, x)
             : launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
     if (profile)
         cudaEventRecord(ctx->ev[2], st);
-    e = f64 ? launch_f64_weights(ds, pl, static_cast<const double *>(qx),
-                                 static_cast<const double *>(qy), sc, ctx->d_err, st)
-            : launch_f32_weights(ds, pl, static_cast<const float *>(qx),
+    e = x     ? launch_f64x_weights(ds, pl, static_cast<const double *>(qx),
+                                    static_cast<const double *>(qy), sc, ctx->d_err, st)
+        : f64 ? launch_f64_weights(ds, pl, static_cast<const double *>(qx),
+                                   static_cast<const double *>(qy), sc, ctx->d_err, st)
+              : launch_f32_weights(ds, pl, static_cast<const float *>(qx),
                                  static_cast<const float *>(qy), sc, ctx->d_err, st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
@@ -433,7 +445,7 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
 size_t culled_extra_bytes(int64_t m, int precision)
 {
     const size_t mm = static_cast<size_t>(m);
-    const size_t es = precision == AIDW_F64 ? sizeof(double) : sizeof(float);
+    const size_t es = f64_arrays(precision) ? sizeof(double) : sizeof(float);
     return 2 * align256(mm * sizeof(uint32_t)) + 2 * align256(mm * es) +
            align256(radix_scratch_bytes(m));
 }
@@ -448,7 +460,8 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
 {
     const AlphaMap am = alpha_map(p);
     const int64_t m = pl.m;
-    const bool f64 = p.precision == AIDW_F64;
+    const bool f64 = f64_arrays(p.precision);
+    const bool xp = p.precision == AIDW_F64X;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
     const size_t b4 = align256(static_cast<size_t>(m) * sizeof(uint32_t));
     const size_t bq = align256(static_cast<size_t>(m) * es);
@@ -470,11 +483,12 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
         ok = ok && launch_f64_knn_cull(ds, pl, sx, sy, p.k, sc, ctx->d_err, st) == cudaSuccess;
         if (profile)
             cudaEventRecord(ctx->ev[1], st);
-        ok = ok && launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
-                       cudaSuccess;
+        ok = ok && launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm,
+                                     xp) == cudaSuccess;
         if (profile)
             cudaEventRecord(ctx->ev[2], st);
-        ok = ok && launch_f64_weights(ds, pl, sx, sy, sc, ctx->d_err, st) == cudaSuccess;
+        ok = ok && (xp ? launch_f64x_weights(ds, pl, sx, sy, sc, ctx->d_err, st)
+                       : launch_f64_weights(ds, pl, sx, sy, sc, ctx->d_err, st)) == cudaSuccess;
         if (profile)
             cudaEventRecord(ctx->ev[3], st);
         ok = ok && launch_f64_finalize(pl, sc, static_cast<double *>(out), st, perm) ==
@@ -550,7 +564,7 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         return AIDW_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return AIDW_ERR_CUDA;
-    const bool f64 = p->precision == AIDW_F64;
+    const bool f64 = f64_arrays(p->precision);
     const size_t es = f64 ? sizeof(double) : sizeof(float);
     const int kq = pointer_kind(qx, ctx->device), kqy = pointer_kind(qy, ctx->device);
     const int ko = pointer_kind(out, ctx->device);

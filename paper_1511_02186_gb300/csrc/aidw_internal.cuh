@@ -28,6 +28,7 @@ constexpr double kEpsF64 = 2.2250738585072014e-308;
 // a coincident point (d2 == eps) and underflows to 0 everywhere else.
 constexpr float kCoincScaleF32 = 1.2676506e30f;  // 2^100
 constexpr double kCoincScaleF64 = 8.452712498170644e270;  // 2^900
+constexpr double kCoincScaleDf = 1.2676506002282294e30;   // 2^100 (AIDW_F64X: float range)
 
 // Bounded waits: an mbarrier wait gives up after this many polls and raises the error word;
 // a wait on another CTA's counter gives up after kMaxWaitPolls polls of at least 256 ns
@@ -97,6 +98,14 @@ struct QParamF64 {
     double c;
 };
 
+// Per-query constants of the AIDW_F64X phase 2: kappa = alpha / 2 (the coincidence scale for a
+// query on a data point) and the nearest squared distance the weights are relative to.
+struct QParamF64X {
+    double kappa;
+    double d1sq;
+};
+static_assert(sizeof(QParamF64X) == sizeof(QParamF64), "shares the FP64 scratch layout");
+
 // Scratch buffers of one interpolation (device memory owned by the library or by the
 // caller of the allocation-free entry point).
 struct Scratch {
@@ -150,7 +159,8 @@ cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *q
                            cudaStream_t st);
 cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
-                              cudaStream_t st, const uint32_t *perm = nullptr);
+                              cudaStream_t st, const uint32_t *perm = nullptr,
+                              bool x_params = false);
 // Phase 1 over Z-ordered FP64 queries, pruned like launch_f32_knn_cull; with pl.with_idx the
 // lists are the k smallest (distance, caller index) pairs, so ties go to the lower index as in
 // the caller-order scan; sqx / sqy are the queries in Z-order and the dataset's points are read
@@ -163,6 +173,11 @@ cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const doubl
                                cudaStream_t st);
 cudaError_t launch_f64_finalize(const Plan &pl, const Scratch &sc, double *out,
                                 cudaStream_t st, const uint32_t *perm = nullptr);
+// AIDW_F64X phase 2 (kernels_f64x.cu); reads QParamF64X written by launch_f64_select with
+// x_params and leaves part_sum in the layout launch_f64_finalize reads.
+cudaError_t launch_f64x_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
+                                const double *qy, const Scratch &sc, int *err,
+                                cudaStream_t st);
 
 // Shape of the kernels: queries per CTA of each scan and the CTA slots per SM that occupancy
 // allows (used to cut splits into whole waves). FP32 shapes follow the tuning fields of
@@ -186,6 +201,8 @@ int f64_knn_queries_per_block(int k);
 int f64_w_queries_per_block();
 int f64_knn_slots_per_sm(int k, bool with_idx);
 int f64_w_slots_per_sm();
+int f64x_w_queries_per_block();
+int f64x_w_slots_per_sm();
 
 // Pipe-rate microbenchmarks (probe.cu).
 cudaError_t run_pipe_probe(int sm_count, aidw_pipe_rates *out);

@@ -412,7 +412,8 @@ __global__ void __launch_bounds__(256)
 f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
                   const double *__restrict__ part_d2, const int32_t *__restrict__ part_idx,
                   QParamF64 *__restrict__ qp, float *__restrict__ out_alpha,
-                  int32_t *__restrict__ out_knn, const uint32_t *__restrict__ perm)
+                  int32_t *__restrict__ out_knn, const uint32_t *__restrict__ perm,
+                  bool x_params)
 {
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= m)
@@ -450,6 +451,19 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     const double R = r_obs / r_exp;           // Eq. 4
     const double mu = membership_eq5(R, am);  // Eq. 5
     const double alpha = alpha_eq6(mu, am);   // Eq. 6
+    if (out_alpha)
+        out_alpha[perm ? perm[q] : q] = static_cast<float>(alpha);
+    if (x_params) {
+        // AIDW_F64X: kappa kept within [2^-100, 2^100] (beyond, the weights are those of the
+        // bounds to far below the tolerance: all equal, or only the nearest points') and the
+        // reference squared distance.
+        QParamF64X x;
+        x.kappa = d1 == 0.0 ? kCoincScaleDf
+                            : fmax(fmin(0.5 * alpha, kCoincScaleDf), 1.0 / kCoincScaleDf);
+        x.d1sq = __dadd_rn(d1, kEpsF64);
+        reinterpret_cast<QParamF64X *>(qp)[q] = x;
+        return;
+    }
     QParamF64 o;
     if (d1 == 0.0) {
         o.neg_s = -kCoincScaleF64;
@@ -460,8 +474,6 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
         o.c = sh * f64math::log2_c(__dadd_rn(d1, kEpsF64));
     }
     qp[q] = o;
-    if (out_alpha)
-        out_alpha[perm ? perm[q] : q] = static_cast<float>(alpha);
 }
 
 template <int Q>
@@ -675,13 +687,13 @@ cudaError_t launch_f64_knn(const DatasetDev &ds, const Plan &pl, const double *q
 
 cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMap &am,
                               const Scratch &sc, float *out_alpha, int32_t *out_knn,
-                              cudaStream_t st, const uint32_t *perm)
+                              cudaStream_t st, const uint32_t *perm, bool x_params)
 {
     const int64_t blocks = (pl.m + 255) / 256;
     f64_select_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         pl.m, pl.knn.splits, k, r_exp, am, static_cast<const double *>(sc.part_d2),
         pl.with_idx ? sc.part_idx : nullptr, static_cast<QParamF64 *>(sc.qparam), out_alpha,
-        out_knn, perm);
+        out_knn, perm, x_params);
     return cudaGetLastError();
 }
 

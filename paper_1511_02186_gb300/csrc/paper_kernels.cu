@@ -355,7 +355,8 @@ extern "C" int aidw_interpolate_paper(aidw_ctx *ctx, aidw_dataset ds, const void
     if (!ctx || !p)
         return AIDW_ERR_INVALID_ARG;
     if ((version != AIDW_VERSION_NAIVE && version != AIDW_VERSION_TILED) ||
-        (layout != AIDW_LAYOUT_SOA && layout != AIDW_LAYOUT_AOAS))
+        (layout != AIDW_LAYOUT_SOA && layout != AIDW_LAYOUT_AOAS) ||
+        p->precision == AIDW_F64X)  // the paper's designs come in FP32 and FP64 only
         return AIDW_ERR_INVALID_ARG;
     DatasetDev dev;
     double r_exp;

@@ -109,17 +109,20 @@ cudaError_t run_one(int sm_count, int blocks_per_sm, float *sink, ProbeTimes *d_
     e = cudaMemcpy(h.data(), d_times, sizeof(ProbeTimes) * blocks, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
         return e;
-    // Every block is resident at once (blocks_per_sm fits), so each SM's elapsed clocks is the
-    // longest block on it; take the median block duration as the per-SM span.
-    std::vector<double> clk(blocks), mh(blocks);
+    // Every block is resident at once (blocks_per_sm fits). A pipe that serves the warps of an
+    // SM unevenly lets some blocks finish early, so the span is the whole launch's, from the
+    // first block's start to the last block's end on the global timer, in clocks at the median
+    // clock rate the blocks observed.
+    std::vector<double> mh(blocks);
+    unsigned long long t0 = h[0].ns0, t1 = h[0].ns1;
     for (int i = 0; i < blocks; ++i) {
-        clk[i] = static_cast<double>(h[i].clk1 - h[i].clk0);
         const double ns = static_cast<double>(h[i].ns1 - h[i].ns0);
-        mh[i] = ns > 0 ? clk[i] / ns * 1e3 : 0.0;
+        mh[i] = ns > 0 ? static_cast<double>(h[i].clk1 - h[i].clk0) / ns * 1e3 : 0.0;
+        t0 = std::min(t0, h[i].ns0);
+        t1 = std::max(t1, h[i].ns1);
     }
-    std::sort(clk.begin(), clk.end());
     std::sort(mh.begin(), mh.end());
-    const double span = clk[blocks / 2];
+    const double span = static_cast<double>(t1 - t0) * mh[blocks / 2] * 1e-3;
     const double iters = OP == 4 ? kIters / 8 : kIters;
     const double ops_per_sm = static_cast<double>(blocks_per_sm) * kProbeThreads * iters * kChains;
     *per_clk_sm = ops_per_sm / span;

@@ -16,6 +16,11 @@ TOL_F64 = 1e-12
 KNN_TIE_REL_F32 = 2e-6
 
 
+def is_f64(precision):
+    """AIDW_F64 and AIDW_F64X take FP64 arrays and share the FP64 parity bar."""
+    return precision in (aidw.F64, aidw.F64X)
+
+
 def oracle_for(wl, precision, q_idx=None, threads=None):
     """Oracle result on the inputs the given path actually sees (FP32-rounded for F32C)."""
     src = wl.as_f32() if precision == aidw.F32C else wl
@@ -36,7 +41,7 @@ def knn_mismatch(knn_gpu, ref, src, precision):
     bad = []
     for q in range(knn_gpu.shape[0]):
         a, b = knn_gpu[q], ref["knn"][q]
-        if precision == aidw.F64:
+        if is_f64(precision):
             if not np.array_equal(a, b):
                 bad.append(q)
             continue
@@ -57,7 +62,7 @@ def knn_mismatch(knn_gpu, ref, src, precision):
 
 def to_device(wl, precision):
     import torch
-    dt = torch.float64 if precision == aidw.F64 else torch.float32
+    dt = torch.float64 if is_f64(precision) else torch.float32
     return (torch.as_tensor(wl.qx, dtype=dt, device="cuda"),
             torch.as_tensor(wl.qy, dtype=dt, device="cuda"))
 
@@ -91,7 +96,7 @@ def assert_parity(ctx, wl, precision, want_knn=True, splits=None, q_idx=None, gp
     if q_idx is not None:
         z, a = z[q_idx], a[q_idx]
         kn = None if kn is None else kn[q_idx]
-    tol = TOL_F64 if precision == aidw.F64 else TOL_F32
+    tol = TOL_F64 if is_f64(precision) else TOL_F32
     err = rel_err(z, ref)
     assert np.all(np.isfinite(z)), "non-finite prediction"
     worst = int(np.argmax(err))
@@ -99,7 +104,7 @@ def assert_parity(ctx, wl, precision, want_knn=True, splits=None, q_idx=None, gp
                               f"(gpu {z[worst]!r}, oracle {ref['z'][worst]!r})")
     # alpha is returned as float: FP32 rounding for the FP64 path; for the FP32 path also the
     # FP32 rounding of r_obs propagated through Eq. 5-6.
-    atol_alpha = (2e-7 if precision == aidw.F64 else 2e-6) * max(wl.levels)
+    atol_alpha = (2e-7 if is_f64(precision) else 2e-6) * max(wl.levels)
     if kn is not None:
         bad = knn_mismatch(kn, ref, src, precision)
         assert not bad, f"{wl.name}: kNN differs at queries {bad[:10]}"

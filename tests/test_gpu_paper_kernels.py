@@ -115,4 +115,7 @@ def test_rejects_bad_arguments(ctx):
             ctx.interpolate_paper(ds, qx, qy, p, version=version, layout=layout)
     with pytest.raises(aidw.AidwError):  # host arrays are not accepted
         ctx.interpolate_paper(ds, qx.cpu(), qy.cpu(), p, out=torch.empty(10))
+    q64 = to_device(wl, aidw.F64)
+    with pytest.raises(aidw.AidwError):  # the paper's designs have no double-float variant
+        ctx.interpolate_paper(ds, *q64, params_of(wl, aidw.F64X))
     ds.destroy()

@@ -2,17 +2,18 @@
 
 FP32 path: Z within 1e-5 relative to max(|Z*|, S*), kNN sets equal up to FP32 distance ties.
 FP64 path: Z within 1e-12, kNN lists bit-identical (same order, ties to the lower index).
+FP64X path (FP64 phase 1, double-float phase 2): the FP64 path's bar.
 """
 import numpy as np
 import pytest
 
 from paper_1511_02186_gb300 import aidw, workloads
-from parity import (TOL_F32, TOL_F64, assert_parity, oracle_for, params_of, rel_err, run_gpu,
-                    to_device)
+from parity import (TOL_F32, TOL_F64, assert_parity, is_f64, oracle_for, params_of, rel_err,
+                    run_gpu, to_device)
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = [aidw.F32C, aidw.F64]
+PRECISIONS = [aidw.F32C, aidw.F64, aidw.F64X]
 
 
 @pytest.fixture(scope="module")
@@ -181,13 +182,35 @@ def test_clustered_grid_sampled(ctx):
     assert ref["alpha"].min() < 1.5 and ref["alpha"].max() > 4.5
 
 
-def test_fp64_paper_scale_sampled_queries(ctx):
-    """FP64 path on the full 1,048,576-point dataset for 4,096 queries: Z within 1e-12 and
+@pytest.mark.parametrize("precision", [aidw.F64, aidw.F64X])
+def test_fp64_paper_scale_sampled_queries(ctx, precision):
+    """FP64 paths on the full 1,048,576-point dataset for 4,096 queries: Z within 1e-12 and
     kNN lists bit-identical."""
     wl = workloads.uniform_paper(0)
     idx = np.random.default_rng(7).choice(wl.m, 4096, replace=False)
     sub = wl.query_subset(idx)
-    assert_parity(ctx, sub, aidw.F64)
+    assert_parity(ctx, sub, precision)
+
+
+def test_fp64x_paper_scale_launch_sampled(ctx):
+    """AIDW_F64X at the benchmark's launch configuration (131,072 queries against the full
+    1,048,576-point dataset: Z-ordered queries, pruned phase 1, split phase 2); 1,024 sampled
+    queries against the oracle, every output finite and inside the range of z."""
+    import torch
+    wl = workloads.uniform_paper(0)
+    qi = np.random.default_rng(8).choice(wl.m, 131072, replace=False)
+    sub = wl.query_subset(qi)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(sub, aidw.F64X)
+    out, a, _ = ctx.interpolate(ds, qx, qy, params_of(sub, aidw.F64X), want_alpha=True)
+    torch.cuda.synchronize()
+    z = out.cpu().numpy()
+    assert np.all(np.isfinite(z)) and z.min() >= wl.z.min() and z.max() <= wl.z.max()
+    idx = np.random.default_rng(9).choice(sub.m, 1024, replace=False)
+    ref, _ = oracle_for(sub, aidw.F64X, idx)
+    assert rel_err(z[idx], ref).max() <= TOL_F64
+    assert np.abs(a.cpu().numpy()[idx] - ref["alpha"]).max() <= 1e-6
+    ds.destroy()
 
 
 # ---- argument and failure handling on the device ---------------------------------------------
@@ -292,6 +315,42 @@ def test_fp64_pruned_knn_equals_caller_order_scan(ctx, idx):
     ds.destroy()
 
 
+@pytest.mark.parametrize("idx", range(5), ids=["uniform", "clustered_k17", "clustered_k32",
+                                               "lattice_ties", "large_offset"])
+def test_fp64x_matches_fp64_path(ctx, idx):
+    """AIDW_F64X shares the FP64 path's phase 1 and selection: alpha and the kNN lists are
+    bit-identical to AIDW_F64's; Z differs only by the double-float phase 2, within 1e-13 of
+    the FP64 path, and both within 1e-12 of the oracle."""
+    import torch
+    wl = _fp64_cases()[idx]
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F64)
+    z64, a64, k64 = ctx.interpolate(ds, qx, qy, params_of(wl, aidw.F64), want_alpha=True,
+                                    want_knn=True)
+    zx, ax, kx = ctx.interpolate(ds, qx, qy, params_of(wl, aidw.F64X), want_alpha=True,
+                                 want_knn=True)
+    zs, _, _ = ctx.interpolate(ds, qx, qy, params_of(wl, aidw.F64X), splits=(3, 5))
+    torch.cuda.synchronize()
+    assert torch.equal(a64, ax) and torch.equal(k64, kx)
+    ref, _ = oracle_for(wl, aidw.F64)
+    for z in (z64, zx, zs):
+        assert rel_err(z.cpu().numpy(), ref).max() <= TOL_F64
+    den = np.maximum(np.abs(z64.cpu().numpy()), ref["scale"])
+    assert (np.abs(zx.cpu().numpy() - z64.cpu().numpy()) / den).max() <= 1e-13
+    ds.destroy()
+
+
+def test_fp64x_extreme_powers(ctx):
+    """Levels up to 40 (weights falling as d^-40 span far more than the float exponent range:
+    the ones below 2^-126 of the nearest point's are dropped) and down to 0.05 (nearly equal
+    weights over the whole dataset): the FP64 bar still holds."""
+    wl = workloads.small_case(98, 20000, 3000, k=10, pattern="clustered", side=400.0,
+                              levels=(0.05, 1.0, 8.0, 20.0, 40.0))
+    assert_parity(ctx, wl, aidw.F64X)
+    ref, _ = oracle_for(wl, aidw.F64X)
+    assert ref["alpha"].min() < 0.5 and ref["alpha"].max() > 30.0
+
+
 @pytest.mark.parametrize("pattern", ["uniform", "clustered"])
 def test_fp32_pruned_knn_equals_split_scan(ctx, pattern):
     """FP32 with enough queries for the pruned phase 1 against the forced split scan: kNN sets
@@ -368,7 +427,7 @@ def test_empty_query_set_and_empty_dataset(ctx, precision):
     import torch
     wl = workloads.small_case(121, 50, 5, k=3)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
-    dt = torch.float64 if precision == aidw.F64 else torch.float32
+    dt = torch.float64 if is_f64(precision) else torch.float32
     e = torch.empty(0, dtype=dt, device="cuda")
     p = aidw.default_params(k=3, precision=precision)
     out, a, kn = ctx.interpolate(ds, e, e, p, want_alpha=True, want_knn=True)
@@ -376,10 +435,10 @@ def test_empty_query_set_and_empty_dataset(ctx, precision):
     assert out.numel() == 0 and a.numel() == 0 and kn.numel() == 0
     out = ctx.idw(ds, e, e, 2.0, precision=precision)
     assert out.numel() == 0
-    h = np.zeros(0, dtype=np.float64 if precision == aidw.F64 else np.float32)
+    h = np.zeros(0, dtype=np.float64 if is_f64(precision) else np.float32)
     out, _, _ = ctx.interpolate(ds, h, h, p)
     assert out.shape == (0,)
-    if precision == aidw.F64:
+    if is_f64(precision):
         rc, rid = ctx.submit(ds, h, h, p, np.zeros(0))
         assert rc == aidw.OK and ctx.wait(rid, 10_000_000) == aidw.OK
         ctx.release(rid)

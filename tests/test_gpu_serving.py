@@ -140,6 +140,9 @@ def test_solo_paths_fp64_and_knn():
         p64 = aidw.default_params(k=10, precision=aidw.F64)
         rc, r1 = ctx.submit(ds, qx, qy, p64, out64)
         assert rc == aidw.OK
+        out64x = np.full(700, np.nan)
+        rc, r3 = ctx.submit(ds, qx, qy, aidw.default_params(k=10, precision=aidw.F64X), out64x)
+        assert rc == aidw.OK
         out32 = np.full(700, np.nan, dtype=np.float32)
         knn = np.full((700, 10), -1, dtype=np.int32)
         rc, r2 = ctx.submit(ds, qx.astype(np.float32), qy.astype(np.float32),
@@ -148,6 +151,8 @@ def test_solo_paths_fp64_and_knn():
         assert ctx.wait(r1, 60_000_000) == aidw.OK and ctx.wait(r2, 60_000_000) == aidw.OK
         ref64, _ = oracle_for(w, aidw.F64)
         assert rel_err(out64, ref64).max() <= TOL_F64
+        assert ctx.wait(r3, 60_000_000) == aidw.OK
+        assert rel_err(out64x, ref64).max() <= TOL_F64
         ref32, _ = oracle_for(w, aidw.F32C)
         assert rel_err(out32, ref32).max() <= TOL_F32
         assert (knn >= 0).all()
