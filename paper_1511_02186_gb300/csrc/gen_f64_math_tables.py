@@ -3,11 +3,12 @@
 both beside this script. Run ``python gen_f64_math_tables.py``.
 
 Method (after Tang's table-driven logarithm and exponential):
-  log2(x): x = 2^e m, m in [1, 2); F = 1 + j/128 from the top 7 bits of m; r = (m - F) / F in
-           [0, 1/128); log2(x) = e + log2(F) + ln(1 + r) / ln 2 with a degree-7 Taylor
-           polynomial for ln(1 + r) (truncation below 2^-59).
-  exp2(y): k = round(64 y), r = y - k/64 in [-1/128, 1/128]; 2^y = 2^(k >> 6) * 2^((k & 63)/64)
-           * e^(r ln 2) with a degree-5 Taylor polynomial (truncation below 4e-17 relative).
+  log2(x): x = 2^e m, m in [1, 2); F = 1 + j/1024 from the top 10 bits of m; r = (m - F) / F
+           in [0, 2^-10); log2(x) = e + log2(F) + ln(1 + r) / ln 2 with a degree-5 Taylor
+           polynomial for ln(1 + r) (truncation below 2^-62).
+  exp2(y): k = round(256 y), r = y - k/256 in [-1/512, 1/512]; 2^y = 2^(k >> 8)
+           * 2^((k & 255)/256) * e^(r ln 2) with a degree-4 Taylor polynomial (truncation below
+           2^-54 relative).
 Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bits):
   log2(x): F = 1 + j/256 from the top 8 bits of the mantissa; u = (m - F) / (F ln 2) by the
            pair (1 / (F ln 2)); log2(1 + r) = u - (ln 2 / 2) u^2 + sum_{i=3..6} c_i u^i with
@@ -102,20 +103,20 @@ def df_tables(ln2):
 
 def main():
     ln2 = mp.log(2)
-    log2_f = [mp.log(1 + mp.mpf(j) / 128) / ln2 for j in range(128)]
-    inv_f = [1 / (1 + mp.mpf(j) / 128) for j in range(128)]
-    exp2_j = [mp.power(2, mp.mpf(j) / 64) for j in range(64)]
-    ln_coef = [mp.mpf((-1) ** (i + 1)) / i for i in range(1, 8)]          # r, r^2 .. r^7
-    exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 6)]          # 1, r ln2 .. r^5
+    log2_f = [mp.log(1 + mp.mpf(j) / 1024) / ln2 for j in range(1024)]
+    inv_f = [1 / (1 + mp.mpf(j) / 1024) for j in range(1024)]
+    exp2_j = [mp.power(2, mp.mpf(j) / 256) for j in range(256)]
+    ln_coef = [mp.mpf((-1) ** (i + 1)) / i for i in range(1, 6)]          # r, r^2 .. r^5
+    exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 5)]          # 1, r ln2 .. r^4
     lines = [
         "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
         "// (values rounded to the nearest double, written as exact hexadecimal literals).",
         table("kLog2F", log2_f),
         table("kInvF", inv_f),
         table("kExp2J", exp2_j),
-        "// ln(1 + r) = sum_{i=1..7} kLnC<i> r^i",
+        "// ln(1 + r) = sum_{i=1..5} kLnC<i> r^i",
         *(f"constexpr double kLnC{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
-        "// e^(r ln 2) = sum_{i=0..5} kExpC<i> r^i",
+        "// e^(r ln 2) = sum_{i=0..4} kExpC<i> r^i",
         *(f"constexpr double kExpC{i} = {lit(c)};" for i, c in enumerate(exp_coef)),
         "constexpr double kInvLn2 = " + lit(1 / ln2) + ";",
         "",
