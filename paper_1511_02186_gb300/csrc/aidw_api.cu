@@ -282,7 +282,10 @@ Plan make_plan(aidw_ctx *ctx, int precision, int64_t n_pad, int64_t m, int k, bo
     // each a rescan of a chunk by a partly idle warp. Measured on GB300 at n = m = 2^20,
     // k = 10, every extra split costs about as much as scanning 100,000 more points.
     pl.knn_slots = ks * ctx->sm_count;
-    pl.knn = plan_pass(m, n_pad, qk, ks * ctx->sm_count, 10000 * k);
+    // The FP64 scan is bound by its FP64 pipe (the exact rescans behind the FP32 prefilter),
+    // which co-resident CTAs share: it is planned as one CTA per SM (measured at n = 1M,
+    // 4,096 queries: 8 splits 24 ms, 37 splits 39 ms).
+    pl.knn = plan_pass(m, n_pad, qk, (f64 ? 1 : ks) * ctx->sm_count, 10000 * k);
     pl.w = plan_pass(m, n_pad, qw, ws * ctx->sm_count, 1024);
     const int64_t G = n_pad / kPadPoints;
     auto force = [&](PassPlan &pp, int S) {
@@ -425,19 +428,21 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
 // more than it saves).
 constexpr int64_t kCullMinQueries = 2048;
 
-// The pruned phase 1 serves both precisions (FP64 lists with indices keep the oracle's tie order
-// by ordering pairs (distance, caller index)) when there are enough queries: with m queries spread over the data, a block of q queries
-// covers about q/m of the area, so each of the m/q blocks visits about n q / (512 m) tiles, and
-// with fewer blocks than the GPU holds (P) the pruned scan takes about n q^2 P / m per-pair
-// steps of one CTA against n m / P steps of each CTA for the split scan: the pruned scan wins
-// when m > q sqrt(P). (Measured at n = 1M, random queries: FP32 split scan faster at m = 8,192,
-// pruned faster at 32,768; FP64 about even at 8,192.)
+// The pruned phase 1 serves every precision (FP64 lists with indices keep the oracle's tie
+// order by ordering pairs (distance, caller index)) when there are enough queries: with m
+// queries spread over the data, a block of q queries covers about q/m of the area, so each of
+// the m/q blocks visits about n q / (512 m) tiles, and with fewer blocks than the GPU holds (P)
+// the pruned scan takes about n q^2 P / m per-pair steps of one CTA against n m / P steps of
+// each CTA for the split scan: the pruned scan wins when m > q sqrt(P). Measured at n = 1M
+// with random queries: in FP32 the split scan is faster at m = 8,192 and the pruned scan at
+// 32,768; in FP64 (both scans with the FP32 prefilter) the split scan at 8,192 (34 against
+// 45 ms) and the pruned scan at 16,384 (38 against 66 ms), so FP64 takes twice the bound.
 bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_idx,
                     const Plan &pl)
 {
-    const double need = kThreads * pl.kq * std::sqrt(static_cast<double>(pl.knn_slots));
-    (void)precision;
     (void)with_idx;
+    const double need = kThreads * pl.kq * std::sqrt(static_cast<double>(pl.knn_slots)) *
+                        (f64_arrays(precision) ? 2.0 : 1.0);
     return ds.n_pad / kTileF32Knn <= kMaxCullTiles && m >= kCullMinQueries &&
            static_cast<double>(m) >= need;
 }

@@ -60,6 +60,19 @@ __device__ __forceinline__ void drain(uint64_t *bar, int t, int ntiles)
         (void)mbar_wait(&bar[u & 1], (u >> 1) & 1);
 }
 
+// FP32 prefilter of the exact FP64 phase-1 scans. Coordinates are taken relative to a centre c
+// and rounded to float. With a = q - c and d the exact distance, the FP32 distance d_f of the
+// rounded coordinates is at least d - 2^-22.5 d - 2^-22.9 |a| (two roundings of each coordinate,
+// one of each difference, one of the sum of squares), so d <= sqrt(T) implies
+// d_f^2 <= (sqrt(T) (1 + 2^-21) + |a| 2^-21)^2: a chunk whose FP32 distances all exceed that holds
+// no point that could enter a list whose k-th squared distance is T, and skips the exact FP64
+// distances (lists are unchanged).
+__device__ __forceinline__ float prefilter_thr(double kth, double ra)
+{
+    const double b = fma(sqrt(kth), 1.0 + 0x1p-21, ra * 0x1p-21);
+    return __double2float_ru(b * b);
+}
+
 template <int KP, int Q, bool IDX>
 __global__ void __launch_bounds__(kThreads)
 f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
@@ -67,6 +80,7 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
                int32_t *__restrict__ part_idx, int *__restrict__ err)
 {
     __shared__ __align__(128) double2 tile[2][kTileF64Knn];
+    __shared__ __align__(16) float2 tilef[kTileF64Knn];  // tile points - c, FP32 (prefilter)
     __shared__ __align__(8) uint64_t bar[2];
     extern __shared__ int32_t idx_smem[];
 
@@ -76,14 +90,23 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
     const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
     const int ntiles = static_cast<int>((p_end - p_begin) / kTileF64Knn);
+    const float4 dbox = *ds.box;  // the prefilter's centre: the dataset box's
+    const double ccx = 0.5 * (static_cast<double>(dbox.x) + static_cast<double>(dbox.z));
+    const double ccy = 0.5 * (static_cast<double>(dbox.y) + static_cast<double>(dbox.w));
 
-    double qxr[Q], qyr[Q];
+    double qxr[Q], qyr[Q], ra[Q];
+    float2 qf[Q];
+    float thr[Q];
     double L[Q][KP];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int64_t q = min(qbase + j * kThreads + tid, m - 1);
         qxr[j] = qx[q];
         qyr[j] = qy[q];
+        const double ax = qxr[j] - ccx, ay = qyr[j] - ccy;
+        qf[j] = make_float2(static_cast<float>(ax), static_cast<float>(ay));
+        ra[j] = sqrt(ax * ax + ay * ay);
+        thr[j] = CUDART_INF_F;
 #pragma unroll
         for (int i = 0; i < KP; ++i)
             L[j][i] = (i < KP - k) ? -CUDART_INF : CUDART_INF;
@@ -120,39 +143,44 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
             break;
         }
         const int64_t pbase = p_begin + static_cast<int64_t>(t) * kTileF64Knn;
+        for (int u = tid; u < kTileF64Knn; u += kThreads) {
+            const double2 p = tile[b][u];
+            tilef[u] = make_float2(static_cast<float>(p.x - ccx), static_cast<float>(p.y - ccy));
+        }
+        __syncthreads();
         for (int c = 0; c < kTileF64Knn; c += kChunkKnn) {
-            double mn[Q];
+            float mn[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                mn[j] = CUDART_INF;
+                mn[j] = CUDART_INF_F;
 #pragma unroll
             for (int u = 0; u < kChunkKnn; ++u) {
-                const double2 p = tile[b][c + u];
-#pragma unroll
-                for (int j = 0; j < Q; ++j)
-                    mn[j] = fmin(mn[j], dist2_exact(qxr[j], qyr[j], p.x, p.y));
-            }
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < Q; ++j)
-                any |= mn[j] < L[j][KP - 1];
-            if (any) {
+                const float2 p = tilef[c + u];
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
-                    if (mn[j] < L[j][KP - 1]) {
+                    const float dx = qf[j].x - p.x, dy = qf[j].y - p.y;
+                    mn[j] = fminf(mn[j], fmaf(dx, dx, dy * dy));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                if (!(mn[j] <= thr[j]))  // (a padding point's FP32 distance is +inf)
+                    continue;
+                bool changed = false;
 #pragma unroll 1
-                        for (int u = 0; u < kChunkKnn; ++u) {
-                            const double2 p = tile[b][c + u];
-                            const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
-                            if (d < L[j][KP - 1]) {
-                                if (IDX)
-                                    index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid,
-                                                     d, static_cast<int32_t>(pbase + c + u));
-                                list_insert<KP>(L[j], d);
-                            }
-                        }
+                for (int u = 0; u < kChunkKnn; ++u) {
+                    const double2 p = tile[b][c + u];
+                    const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
+                    if (d < L[j][KP - 1]) {
+                        if (IDX)
+                            index_insert<KP>(L[j], idx_smem + j * KP * kThreads + tid, d,
+                                             static_cast<int32_t>(pbase + c + u));
+                        list_insert<KP>(L[j], d);
+                        changed = true;
                     }
                 }
+                if (changed)
+                    thr[j] = prefilter_thr(L[j][KP - 1], ra[j]);
             }
         }
         __syncthreads();
@@ -232,6 +260,7 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
 {
     extern __shared__ unsigned long long order[];  // [ntiles_p2] sort keys
     __shared__ __align__(16) double2 tile[kTileF32Knn];
+    __shared__ __align__(16) float2 tilef[kTileF32Knn];  // tile points - block centre, FP32
     __shared__ int32_t tidx[IDX ? kTileF32Knn : 1];  // caller index of each tile point
     constexpr int W = kThreads / 32;
     __shared__ double red[4][W];
@@ -292,8 +321,20 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
     }
     __syncthreads();
     const double qx0 = sbox[0], qy0 = sbox[1], qx1 = sbox[2], qy1 = sbox[3];
-    const float qcx = static_cast<float>(0.5 * (qx0 + qx1));
-    const float qcy = static_cast<float>(0.5 * (qy0 + qy1));
+    const double ccx = 0.5 * (qx0 + qx1), ccy = 0.5 * (qy0 + qy1);
+    const float qcx = static_cast<float>(ccx);
+    const float qcy = static_cast<float>(ccy);
+    // FP32 prefilter (prefilter_thr) with the block's centre as c.
+    float2 qf[Q];
+    double ra[Q];
+    float thr[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const double ax = qxr[j] - ccx, ay = qyr[j] - ccy;
+        qf[j] = make_float2(static_cast<float>(ax), static_cast<float>(ay));
+        ra[j] = sqrt(ax * ax + ay * ay);
+        thr[j] = CUDART_INF_F;
+    }
     // Keys: bound rounded down to FP32 (32 bits), centre distance (19 bits), tile (13 bits).
     for (int t = tid; t < ntiles_p2; t += kThreads) {
         unsigned long long key = ~0ull;
@@ -333,7 +374,9 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
         const int64_t t = static_cast<int64_t>(key & 0x1fffull);
         for (int u = tid; u < kTileF32Knn; u += kThreads) {
             const int32_t o = ds.orig[t * kTileF32Knn + u];
-            tile[u] = o >= 0 ? ds.xy64[o] : make_double2(CUDART_INF, CUDART_INF);
+            const double2 p = o >= 0 ? ds.xy64[o] : make_double2(CUDART_INF, CUDART_INF);
+            tile[u] = p;
+            tilef[u] = make_float2(static_cast<float>(p.x - ccx), static_cast<float>(p.y - ccy));
             if (IDX)
                 tidx[u] = o;
         }
@@ -341,35 +384,43 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
         const double wlb = box_bound64(ds.tile_box[t], wx0, wy0, wx1, wy1);
         if (!(wlb > wthr)) {  // a tie needs d == wthr, and the bound is strictly below d
             for (int c = 0; c < kTileF32Knn; c += kChunkKnn) {
-                double mn[Q];
+                float mn[Q];
 #pragma unroll
                 for (int j = 0; j < Q; ++j)
-                    mn[j] = CUDART_INF;
+                    mn[j] = CUDART_INF_F;
 #pragma unroll
                 for (int u = 0; u < kChunkKnn; ++u) {
-                    const double2 p = tile[c + u];
+                    const float2 p = tilef[c + u];
 #pragma unroll
-                    for (int j = 0; j < Q; ++j)
-                        mn[j] = fmin(mn[j], dist2_exact(qxr[j], qyr[j], p.x, p.y));
+                    for (int j = 0; j < Q; ++j) {
+                        const float dx = qf[j].x - p.x, dy = qf[j].y - p.y;
+                        mn[j] = fminf(mn[j], fmaf(dx, dx, dy * dy));
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
-                    // With indices a tie with the k-th distance may still enter (lower index).
-                    if (IDX ? mn[j] <= L[j][KP - 1] : mn[j] < L[j][KP - 1]) {
+                    if (!(mn[j] <= thr[j]))  // (a padding point's FP32 distance is +inf or NaN)
+                        continue;
+                    // The exact scan of the chunk; with indices a tie with the k-th distance may
+                    // still enter (lower index).
+                    bool changed = false;
 #pragma unroll 1
-                        for (int u = 0; u < kChunkKnn; ++u) {
-                            const double2 p = tile[c + u];
-                            const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
-                            if constexpr (IDX) {
-                                const int32_t id = tidx[c + u];
-                                if (d < L[j][KP - 1] ||
-                                    (d == L[j][KP - 1] && id < I[j][KP - 1]))
-                                    pair_insert<KP>(L[j], I[j], d, id);
-                            } else if (d < L[j][KP - 1]) {
-                                list_insert<KP>(L[j], d);
+                    for (int u = 0; u < kChunkKnn; ++u) {
+                        const double2 p = tile[c + u];
+                        const double d = dist2_exact(qxr[j], qyr[j], p.x, p.y);
+                        if constexpr (IDX) {
+                            const int32_t id = tidx[c + u];
+                            if (d < L[j][KP - 1] || (d == L[j][KP - 1] && id < I[j][KP - 1])) {
+                                pair_insert<KP>(L[j], I[j], d, id);
+                                changed = true;
                             }
+                        } else if (d < L[j][KP - 1]) {
+                            list_insert<KP>(L[j], d);
+                            changed = true;
                         }
                     }
+                    if (changed)
+                        thr[j] = prefilter_thr(L[j][KP - 1], ra[j]);
                 }
             }
         }

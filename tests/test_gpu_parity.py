@@ -263,16 +263,16 @@ def test_budget_and_injected_allocation_failure(ctx):
 
 def _fp64_cases():
     rng = np.random.default_rng(91)
-    # Enough queries (m > block size x sqrt(resident blocks)) for the pruned phase 1.
-    cases = [workloads.small_case(92, 30011, 12003, k=10, pattern="uniform", side=800.0),
-             workloads.small_case(93, 50000, 12288, k=17, pattern="clustered", side=300.0),
+    # Enough queries (in FP64, m > 2 x block size x sqrt(resident blocks)) for the pruned phase 1.
+    cases = [workloads.small_case(92, 30011, 16411, k=10, pattern="uniform", side=800.0),
+             workloads.small_case(93, 50000, 16384, k=17, pattern="clustered", side=300.0),
              workloads.small_case(94, 20000, 9000, k=32, pattern="clustered", side=50.0)]
     # Integer lattice (exact ties everywhere), queries on half-integers and on points.
     g = np.arange(60, dtype=float)
     gx, gy = np.meshgrid(g, g)
     perm = rng.permutation(3600)
-    qx = rng.integers(0, 120, 12000) / 2.0
-    qy = rng.integers(0, 120, 12000) / 2.0
+    qx = rng.integers(0, 120, 16384) / 2.0
+    qy = rng.integers(0, 120, 16384) / 2.0
     cases.append(workloads.Workload("lattice64", gx.ravel()[perm], gy.ravel()[perm],
                                     rng.standard_normal(3600), 3600.0, qx, qy, k=9))
     # Large coordinates with small spacing: FP32 rounding moves points by up to 1/16, far more
@@ -280,8 +280,8 @@ def _fp64_cases():
     x = 1.0e6 + rng.uniform(0, 40, 30000)
     y = -2.0e6 + rng.uniform(0, 40, 30000)
     cases.append(workloads.Workload("offset", x, y, rng.standard_normal(30000), 1600.0,
-                                    1.0e6 + rng.uniform(0, 40, 12000),
-                                    -2.0e6 + rng.uniform(0, 40, 12000), k=10))
+                                    1.0e6 + rng.uniform(0, 40, 16384),
+                                    -2.0e6 + rng.uniform(0, 40, 16384), k=10))
     return cases
 
 
