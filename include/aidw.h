@@ -54,7 +54,7 @@ extern "C" {
  * FP64 path's phase 1, neighbour lists and alpha; in phase 2 each pair's squared distance is
  * formed in FP64 and the rest of its work (log2, the power of Eq. 1, both weighted sums) runs
  * in double-float arithmetic (pairs of floats, about 48 bits) on the FP32 pipes, which on
- * GB300 run at about 90 times the FP64 rate. Results agree with the FP64 path to about 1e-13
+ * GB300 run at 64 times the FP64 rate. Results agree with the FP64 path to about 1e-13
  * relative to max(|Z|, sum w|z| / sum w); weights below 2^-126 of the nearest point's are
  * dropped. */
 #define AIDW_F32C 0

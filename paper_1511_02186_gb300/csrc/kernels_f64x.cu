@@ -1,7 +1,7 @@
 // AIDW_F64X phase 2 for sm_103a: Eq. 1 over all data points with FP64 inputs and output, the
 // squared distance formed in FP64 exactly as the FP64 path forms it, and the rest of each pair's
 // work (log2, the adaptive power, exp2, both weighted sums) in double-float arithmetic on the
-// FP32 pipes (df_math.cuh). GB300 runs FP64 at about 1/90 of its FP32 rate, so the four FP64
+// FP32 pipes (df_math.cuh). GB300 runs FP64 at 1/64 of its FP32 rate, so the four FP64
 // operations of the distance bound this scan and the hundred-odd FP32 operations per pair run
 // beside them. Phase 1, the selection of alpha (Eq. 2-6) and the final division stay the FP64
 // path's kernels.
