@@ -286,6 +286,32 @@ def bench_batched(ctx, steps: int, warmup: int, dev, stream):
                       "kernel shape chosen by the autotuner on this batch"}
 
 
+def bench_standard_idw(ctx, ds, wl, dev, stream, peak):
+    """Standard IDW (Eq. 1 with one constant power, the paper's comparison method) on the 1M
+    dataset for 262,144 seeded queries, FP32 path: one warm-up and three timed calls of
+    aidw_idw (a one-neighbour phase 1 for the normalising distance and the coincidence test,
+    then phase 2 over all points), reported against the phase-2 bound."""
+    import torch
+    from paper_1511_02186_gb300 import aidw
+    q = 262144
+    idx = torch.as_tensor(np.random.default_rng(11).choice(wl.m, q, replace=False))
+    qx = torch.as_tensor(wl.qx, dtype=torch.float32, device=dev)[idx.to(dev)].contiguous()
+    qy = torch.as_tensor(wl.qy, dtype=torch.float32, device=dev)[idx.to(dev)].contiguous()
+    out = torch.empty(q, dtype=torch.float32, device=dev)
+    ctx.idw(ds, qx, qy, 2.0, aidw.F32C, out=out, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        ctx.idw(ds, qx, qy, 2.0, aidw.F32C, out=out, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    value = q * wl.n / (ms / 1e3)
+    return {"workload": f"uniform_{wl.n}_x_{q}", "power": 2.0, "precision": "f32",
+            "ms": ms, "value": value, "unit": UNIT, "frac_of_phase2_bound": value / peak}
+
+
 def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s: float):
     """64 resident datasets (n log-uniform in [16K, 1M]); Poisson arrivals of requests with
     256..262,144 query points (log-uniform, host arrays) uniform in the dataset's square.
@@ -676,6 +702,7 @@ def run_gpu(args):
     batched = bench_batched(ctx, max(2, args.steps), args.warmup, dev, stream)
     stress = bench_precision_stress(ctx, dev, stream)
     designs = bench_paper_designs(ctx, dev, stream)
+    idw = bench_standard_idw(ctx, ds, wl, dev, stream, peak)
     served = None
     if world == 1 or rank == 0:
         sctx = aidw.Context(local)
@@ -769,6 +796,7 @@ def run_gpu(args):
             "batched": batched,
             "precision_stress": stress,
             "paper_kernel_designs": designs,
+            "standard_idw": idw,
             "served": served,
             "gpu_launches": sum(t.launches for t in ktimes),
             "clocks": clk,
