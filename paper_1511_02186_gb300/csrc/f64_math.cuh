@@ -4,15 +4,16 @@
 //
 //   log2(x), x a positive normal double or +inf: x = 2^e m with m in [1, 2); F = 1 + j/1024 from
 //     the top 10 bits of m (exact); r = (m - F) / F in [0, 2^-10) (m - F exact, one rounding in
-//     the product with 1/F); log2(x) = e + (log2 F + ln(1 + r) / ln 2), the logarithm by its
-//     degree-5 Taylor polynomial. Absolute error about one ulp of max(1, |log2 x|).
+//     the product with 1/F); log2(x) = e + (log2 F + log2(1 + r)), the logarithm by the
+//     degree-5 Taylor polynomial of ln(1 + r) / ln 2, its last step adding log2 F. Absolute
+//     error about one ulp of max(1, |log2 x|).
 //   exp2(y), y < 1023: y <= -1021 gives 0 (far below any weight that matters next to the nearest
 //     point's, which is 1); else k = round(256 y) by the 1.5 * 2^52 rounding constant,
 //     r = y - k/256 in [-1/512, 1/512] (exact), 2^y = 2^(k >> 8) * 2^((k & 255)/256)
 //     * e^(r ln 2) with a degree-4 Taylor polynomial; the power of two is added to the exponent
 //     field. Relative error a few ulps.
 // The range tests read the operands' bits on the integer pipe, so that the FP64 pipe, GB300's
-// scarcest, runs only the arithmetic: 9 and 8 double-precision operations, against several
+// scarcest, runs only the arithmetic: 8 and 8 double-precision operations, against several
 // times that for the general library functions; the weights of Eq. 1 need the absolute accuracy
 // of log2 (it is scaled by alpha / 2 and exponentiated), which these keep.
 #pragma once
@@ -55,13 +56,12 @@ __device__ __forceinline__ double log2_finish(double x, double log2f, double inv
     const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
     const double F = __longlong_as_double((b & 0x000FFC0000000000LL) | 0x3FF0000000000000LL);
     const double r = __dmul_rn(__dsub_rn(m, F), invf);
-    double p = __fma_rn(kLnC5, r, kLnC4);
-    p = __fma_rn(p, r, kLnC3);
-    p = __fma_rn(p, r, kLnC2);
-    p = __fma_rn(p, r, kLnC1);
-    p = __dmul_rn(p, r);
+    double p = __fma_rn(kL2C5, r, kL2C4);
+    p = __fma_rn(p, r, kL2C3);
+    p = __fma_rn(p, r, kL2C2);
+    p = __fma_rn(p, r, kL2C1);
     const double e = static_cast<double>(static_cast<int>(b >> 52) - 1023);
-    const double v = __dadd_rn(e, __fma_rn(p, kInvLn2, log2f));
+    const double v = __dadd_rn(e, __fma_rn(p, r, log2f));
     return ((b >> 52) & 0x7FF) == 0x7FF ? CUDART_INF : v;  // +inf, and NaN (as +inf)
 }
 

@@ -4,8 +4,8 @@ both beside this script. Run ``python gen_f64_math_tables.py``.
 
 Method (after Tang's table-driven logarithm and exponential):
   log2(x): x = 2^e m, m in [1, 2); F = 1 + j/1024 from the top 10 bits of m; r = (m - F) / F
-           in [0, 2^-10); log2(x) = e + log2(F) + ln(1 + r) / ln 2 with a degree-5 Taylor
-           polynomial for ln(1 + r) (truncation below 2^-62).
+           in [0, 2^-10); log2(x) = e + log2(F) + log2(1 + r) with the degree-5 Taylor
+           polynomial of ln(1 + r) divided by ln 2 (truncation below 2^-62).
   exp2(y): k = round(256 y), r = y - k/256 in [-1/512, 1/512]; 2^y = 2^(k >> 8)
            * 2^((k & 255)/256) * e^(r ln 2) with a degree-4 Taylor polynomial (truncation below
            2^-54 relative).
@@ -106,7 +106,7 @@ def main():
     log2_f = [mp.log(1 + mp.mpf(j) / 1024) / ln2 for j in range(1024)]
     inv_f = [1 / (1 + mp.mpf(j) / 1024) for j in range(1024)]
     exp2_j = [mp.power(2, mp.mpf(j) / 256) for j in range(256)]
-    ln_coef = [mp.mpf((-1) ** (i + 1)) / i for i in range(1, 6)]          # r, r^2 .. r^5
+    ln_coef = [mp.mpf((-1) ** (i + 1)) / i / ln2 for i in range(1, 6)]    # r, r^2 .. r^5
     exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 5)]          # 1, r ln2 .. r^4
     lines = [
         "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
@@ -114,11 +114,10 @@ def main():
         table("kLog2F", log2_f),
         table("kInvF", inv_f),
         table("kExp2J", exp2_j),
-        "// ln(1 + r) = sum_{i=1..5} kLnC<i> r^i",
-        *(f"constexpr double kLnC{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
+        "// log2(1 + r) = sum_{i=1..5} kL2C<i> r^i",
+        *(f"constexpr double kL2C{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
         "// e^(r ln 2) = sum_{i=0..4} kExpC<i> r^i",
         *(f"constexpr double kExpC{i} = {lit(c)};" for i, c in enumerate(exp_coef)),
-        "constexpr double kInvLn2 = " + lit(1 / ln2) + ";",
         "",
     ]
     path = os.path.join(HERE, "f64_math_tables.inc")
