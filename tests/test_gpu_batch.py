@@ -157,9 +157,10 @@ def test_batch_edge_cases(ctx):
     with pytest.raises(aidw.AidwError):  # host output array
         ctx.interpolate_batch([(ds, qx, qx, aidw.default_params(k=3),
                                 torch.empty(10, dtype=torch.float32), None)])
-    with pytest.raises(aidw.AidwError):  # F64 is not batched
-        ctx.interpolate_batch([(ds, qx, qx, aidw.default_params(k=3, precision=aidw.F64),
-                                torch.empty(10, dtype=torch.float32, device="cuda"), None)])
+    for prec in (aidw.F64, aidw.F64X):  # only the FP32 path is batched
+        with pytest.raises(aidw.AidwError):
+            ctx.interpolate_batch([(ds, qx, qx, aidw.default_params(k=3, precision=prec),
+                                    torch.empty(10, dtype=torch.float32, device="cuda"), None)])
     ds.destroy()
 
 

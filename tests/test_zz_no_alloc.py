@@ -74,6 +74,7 @@ def test_noalloc_rejects_what_it_cannot_do():
                                               hq.ctypes.data, 10, ctypes.byref(p),
                                               hq.ctypes.data, None)
         assert rc == aidw.ERR_INVALID_ARG
-        p64 = aidw.default_params(k=10, precision=aidw.F64)
-        assert _noalloc(ctx, ds, qx[:10], qy[:10], p64, out) == aidw.ERR_INVALID_ARG
+        for prec in (aidw.F64, aidw.F64X):
+            p64 = aidw.default_params(k=10, precision=prec)
+            assert _noalloc(ctx, ds, qx[:10], qy[:10], p64, out) == aidw.ERR_INVALID_ARG
         ds.destroy()
