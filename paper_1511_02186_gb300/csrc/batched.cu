@@ -301,12 +301,27 @@ int batch_grid(int sm_count, size_t dyn, int qw, int ctas_per_sm)
 }  // namespace
 
 // Phase-1 plan of a batch item: one pruned unit per query block when the dataset's tile order
-// fits in shared memory, else split scans.
+// fits in shared memory and the item has enough queries, else split scans. A pruned unit visits
+// the tiles near its block's queries; with few queries spread over the data that is most of
+// the tiles, scanned by one CTA (m = 256 against 800,000 points: 19 ms as one pruned unit, 5 ms
+// as split scans), so an item with fewer than kBatchCullMinQueries queries scans instead, its
+// data cut into enough splits for about kBatchKnnUnits units in all. Above that the pruned
+// units do several times less work than a scan of every pair, which a batch's throughput
+// needs (the 256-dataset batch: 80.5 ms with the pruned units from 1,024 queries on, 83.5 ms
+// from 4,096 on).
+constexpr int64_t kBatchCullMinQueries = 1024;
+constexpr int64_t kBatchKnnUnits = 128;
+
 PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, int kq, bool *cull)
 {
-    *cull = n_pad / kTileF32Knn <= kMaxCullTiles;
+    *cull = n_pad / kTileF32Knn <= kMaxCullTiles && m >= kBatchCullMinQueries;
     const int qk = kThreads * (*cull ? kq : (kp <= 16 ? 4 : 2));
-    return batch_pass(m, n_pad, qk, *cull ? n_pad : kBatchKnnSplit);
+    if (*cull)
+        return batch_pass(m, n_pad, qk, n_pad);
+    const int64_t qblocks = std::max<int64_t>(1, (m + qk - 1) / qk);
+    const int64_t splits = std::max<int64_t>(1, kBatchKnnUnits / qblocks);
+    const int64_t target = std::max<int64_t>(kPadPoints, (n_pad + splits - 1) / splits);
+    return batch_pass(m, n_pad, qk, std::min<int64_t>(target, kBatchKnnSplit));
 }
 
 size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config &cfg)
