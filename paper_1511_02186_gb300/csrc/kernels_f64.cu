@@ -2,7 +2,10 @@
 // every step in double precision (Sec. 3.2.1 builds its kernels for float and double alike).
 // Squared distances of phase 1 are formed as dx*dx + dy*dy with each product and sum rounded
 // separately, so neighbour lists agree bit for bit with a reference that evaluates the same
-// expression in IEEE double without fused multiply-add. Ties go to the lower index.
+// expression in IEEE double without fused multiply-add. Ties go to the lower index. Both
+// phase-1 scans put an FP32 prefilter in front of those exact distances (prefilter_thr): a
+// 16-point chunk is scanned exactly only when one of its FP32 distances could be within the
+// query's k-th distance, which keeps the lists exact while most pairs cost FP32 work only.
 #include <math_constants.h>
 
 #include "aidw_internal.cuh"
@@ -221,7 +224,9 @@ f64_knn_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__
 // the caller-order FP64 copy through the Z-order map. The tile boxes hold the FP32 coordinates;
 // widened by 2^-23 of their largest magnitude they contain the FP64 points (FP32 rounding moves a
 // coordinate by at most 2^-24 of it), and the bound is shrunk by 2^-50 to cover its own rounding
-// and that of the exact distance, so no skipped point could have entered a list.
+// and that of the exact distance, so no skipped point could have entered a list. Inside a
+// visited tile the FP32 prefilter (centre: the block's query box) decides which chunks get the
+// exact distances.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double box_bound64(float4 tb, double qx0, double qy0, double qx1,
                                               double qy1)
