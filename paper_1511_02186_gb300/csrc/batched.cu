@@ -312,6 +312,23 @@ int batch_grid(int sm_count, size_t dyn, int qw, int ctas_per_sm)
 constexpr int64_t kBatchCullMinQueries = 1024;
 constexpr int64_t kBatchKnnUnits = 128;
 
+// Phase-2 plan of a batch item: data splits of at most split_points points, and, for an item
+// with few queries, enough of them for about kBatchMinWeightUnits units of 256 queries, so
+// that an item alone (a lightly loaded server's flight) still spreads over every SM (a request
+// of 8,192 queries against 231,679 points with 65,536-point splits: 128 units for 608 resident
+// CTAs; served in 5.3 ms, with the extra splits in 2.7 ms, the one-shot call 2.5 ms). The split
+// length depends on the item's sizes and split_points only (not on the rest of the batch, nor
+// on the arithmetic-neutral shape fields).
+constexpr int64_t kBatchMinWeightUnits = 1024;
+
+PassPlan batch_w_plan(int64_t m, int64_t n_pad, int qpb, int64_t split_points)
+{
+    const int64_t blocks256 = std::max<int64_t>(1, (m + 255) / 256);
+    const int64_t want = (kBatchMinWeightUnits + blocks256 - 1) / blocks256;
+    const int64_t target = std::max<int64_t>(kPadPoints, (n_pad + want - 1) / want);
+    return batch_pass(m, n_pad, qpb, std::min<int64_t>(split_points, target));
+}
+
 PassPlan batch_knn_plan(int64_t m, int64_t n_pad, int kp, int kq, bool *cull)
 {
     *cull = n_pad / kTileF32Knn <= kMaxCullTiles && m >= kBatchCullMinQueries;
@@ -330,8 +347,8 @@ size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config 
     const int kp = kp_for(k, cfg.knn_list);
     const PassPlan pk = batch_knn_plan(m, n_pad, kp, cull_queries_per_thread(kp,
                                        cfg.knn_queries_per_thread), &cull);
-    const PassPlan pw = batch_pass(m, n_pad, kThreads * cfg.queries_per_thread,
-                                   cfg.split_points);
+    const PassPlan pw = batch_w_plan(m, n_pad, kThreads * cfg.queries_per_thread,
+                                     cfg.split_points);
     const size_t mm = static_cast<size_t>(m);
     return align256(pk.splits * static_cast<size_t>(k) * mm * sizeof(float)) +
            align256(mm * sizeof(QParamF32)) + align256(pw.splits * 4 * mm * sizeof(float)) +
@@ -384,7 +401,7 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.am = alpha_map(b.params);
         bool cull;
         d.knn = batch_knn_plan(b.m, dev.n_pad, d.kp, d.kq, &cull);
-        d.w = batch_pass(b.m, dev.n_pad, kThreads * cfg.queries_per_thread, cfg.split_points);
+        d.w = batch_w_plan(b.m, dev.n_pad, kThreads * cfg.queries_per_thread, cfg.split_points);
         d.ntiles = static_cast<int32_t>(dev.n_pad / kTileF32Knn);
         int p2 = 1;
         while (p2 < d.ntiles)
