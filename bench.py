@@ -735,7 +735,8 @@ def run_gpu(args):
                           "finalize": kf},
             "plan": {"knn_splits": ktimes[0].splits, "w_splits": ktimes[0].weight_splits,
                      "query_blocks": ktimes[0].query_blocks},
-            "roofline": {"bound": "alu", "kernel": (f"f32_{dominant}_kernel<{shape.queries_per_thread}, "
+            "roofline": {"bound": "alu",
+                         "kernel": (f"f32_{dominant}_kernel<{shape.queries_per_thread}, "
                                     f"{shape.tile_points}>"),
                          "achieved": achieved, "peak": peak, "unit": UNIT,
                          "frac": achieved / peak,

@@ -17,8 +17,8 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(aidw_[a-z0-9_]+)\s*\(",
-                             text, flags=re.M):
+        decl = r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(aidw_[a-z0-9_]+)\s*\("
+        for m in re.finditer(decl, text, flags=re.M):
             names.add(m.group(1))
     return names
 
