@@ -372,6 +372,45 @@ AlphaMap alpha_map(const aidw_params &p)
     return am;
 }
 
+// Phase boundaries of one interpolation: the profiling events (when profiling is on) and NVTX
+// ranges naming the phases, so that a profiler can attribute the kernels launched in each (for
+// example `ncu --nvtx --nvtx-include "aidw phase 2/"`). The ranges span the host-side enqueue;
+// without a tool attached the NVTX calls do nothing.
+class PhaseMarks {
+  public:
+    PhaseMarks(aidw_ctx *ctx, cudaStream_t st, bool profile)
+        : ctx_(ctx), st_(st), profile_(profile)
+    {
+    }
+    PhaseMarks(const PhaseMarks &) = delete;
+    PhaseMarks &operator=(const PhaseMarks &) = delete;
+    ~PhaseMarks()
+    {
+        if (open_)
+            nvtxRangePop();
+    }
+    // Boundary i: the start of phase i (0 phase 1, with the query ordering; 1 selection;
+    // 2 phase 2; 3 finalisation), 4 the end.
+    void at(int i)
+    {
+        static const char *const kNames[4] = {"aidw phase 1", "aidw select", "aidw phase 2",
+                                              "aidw finalize"};
+        if (profile_)
+            cudaEventRecord(ctx_->ev[i], st_);
+        if (open_)
+            nvtxRangePop();
+        open_ = i < 4;
+        if (open_)
+            nvtxRangePushA(kNames[i]);
+    }
+
+  private:
+    aidw_ctx *ctx_;
+    cudaStream_t st_;
+    bool profile_;
+    bool open_ = false;
+};
+
 // Enqueues the four kernels of one interpolation on `st` with device arrays only.
 int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
                           const aidw_params &p, const void *qx, const void *qy,
@@ -382,22 +421,20 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
     cudaError_t e;
     const bool f64 = f64_arrays(p.precision);
     const bool x = p.precision == AIDW_F64X;
-    if (profile)
-        cudaEventRecord(ctx->ev[0], st);
+    PhaseMarks marks(ctx, st, profile);
+    marks.at(0);
     e = f64 ? launch_f64_knn(ds, pl, static_cast<const double *>(qx),
                              static_cast<const double *>(qy), p.k, sc, ctx->d_err, st)
             : launch_f32_knn(ds, pl, static_cast<const float *>(qx),
                              static_cast<const float *>(qy), p.k, sc, ctx->d_err, st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
-    if (profile)
-        cudaEventRecord(ctx->ev[1], st);
+    marks.at(1);
     e = f64 ? launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, nullptr, x)
             : launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
-    if (profile)
-        cudaEventRecord(ctx->ev[2], st);
+    marks.at(2);
     e = x     ? launch_f64x_weights(ds, pl, static_cast<const double *>(qx),
                                     static_cast<const double *>(qy), sc, ctx->d_err, st)
         : f64 ? launch_f64_weights(ds, pl, static_cast<const double *>(qx),
@@ -406,14 +443,13 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
                                  static_cast<const float *>(qy), sc, ctx->d_err, st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
-    if (profile)
-        cudaEventRecord(ctx->ev[3], st);
+    marks.at(3);
     e = f64 ? launch_f64_finalize(pl, sc, static_cast<double *>(out), st)
             : launch_f32_finalize(pl, sc, static_cast<float *>(out), st);
     if (e != cudaSuccess)
         return AIDW_ERR_CUDA;
+    marks.at(4);
     if (profile) {
-        cudaEventRecord(ctx->ev[4], st);
         ctx->last = aidw_kernel_times{};
         ctx->last.splits = pl.knn.splits;
         ctx->last.query_blocks = pl.knn.qblocks;
@@ -476,8 +512,8 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
     void *sqx = e + 2 * b4;
     void *sqy = e + 2 * b4 + bq;
     void *sort_tmp = e + 2 * b4 + 2 * bq;
-    if (profile)
-        cudaEventRecord(ctx->ev[0], st);
+    PhaseMarks marks(ctx, st, profile);
+    marks.at(0);
     bool ok;
     if (f64) {
         const double *x = static_cast<const double *>(qx), *y = static_cast<const double *>(qy);
@@ -486,16 +522,13 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
         ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
         ok = ok && gather_queries_f64(x, y, perm, m, sx, sy, st) == cudaSuccess;
         ok = ok && launch_f64_knn_cull(ds, pl, sx, sy, p.k, sc, ctx->d_err, st) == cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[1], st);
+        marks.at(1);
         ok = ok && launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm,
                                      xp) == cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[2], st);
+        marks.at(2);
         ok = ok && (xp ? launch_f64x_weights(ds, pl, sx, sy, sc, ctx->d_err, st)
                        : launch_f64_weights(ds, pl, sx, sy, sc, ctx->d_err, st)) == cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[3], st);
+        marks.at(3);
         ok = ok && launch_f64_finalize(pl, sc, static_cast<double *>(out), st, perm) ==
                        cudaSuccess;
     } else {
@@ -505,22 +538,19 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
         ok = ok && radix_sort_pairs(keys, perm, m, sort_tmp, st) == cudaSuccess;
         ok = ok && gather_queries(x, y, perm, m, sx, sy, st) == cudaSuccess;
         ok = ok && launch_f32_knn_cull(ds, pl, sx, sy, p.k, sc, ctx->d_err, st) == cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[1], st);
+        marks.at(1);
         ok = ok && launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, perm) ==
                        cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[2], st);
+        marks.at(2);
         ok = ok && launch_f32_weights(ds, pl, sx, sy, sc, ctx->d_err, st) == cudaSuccess;
-        if (profile)
-            cudaEventRecord(ctx->ev[3], st);
+        marks.at(3);
         ok = ok && launch_f32_finalize(pl, sc, static_cast<float *>(out), st, perm) ==
                        cudaSuccess;
     }
     if (!ok)
         return AIDW_ERR_CUDA;
+    marks.at(4);
     if (profile) {
-        cudaEventRecord(ctx->ev[4], st);
         ctx->last = aidw_kernel_times{};
         ctx->last.splits = pl.knn.splits;
         ctx->last.query_blocks = pl.knn.qblocks;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <mutex>
 #include <vector>
@@ -12,6 +13,22 @@
 struct aidw_ctx;
 
 namespace aidw {
+
+// NVTX range over a scope: names the host-side enqueue interval, to which a profiler attributes
+// the kernels launched inside it; a no-op without a tool attached.
+class NvtxScope {
+  public:
+    explicit NvtxScope(const char *name)
+    {
+        nvtxRangePushA(name);
+    }
+    ~NvtxScope()
+    {
+        nvtxRangePop();
+    }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 struct ServingRuntime;
 

@@ -546,6 +546,7 @@ int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st)
 {
     if (bs.n_units == 0)
         return AIDW_OK;
+    NvtxScope range("aidw batch");
     const BatchItemDev *items = static_cast<const BatchItemDev *>(bs.d_items);
     const int64_t tq = bs.total_q;
     const unsigned gx = static_cast<unsigned>(std::min<int64_t>((bs.max_m + 255) / 256, 64));
@@ -697,6 +698,7 @@ int aidw_batch_launch(aidw_ctx *ctx, aidw_batch *b, void *stream)
         return AIDW_ERR_INVALID_ARG;
     if (b->st.n_units == 0)
         return AIDW_OK;
+    NvtxScope range("aidw batch");
     return cudaGraphLaunch(b->st.graph, static_cast<cudaStream_t>(stream)) == cudaSuccess
                ? AIDW_OK
                : AIDW_ERR_CUDA;

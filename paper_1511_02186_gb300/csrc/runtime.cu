@@ -141,6 +141,7 @@ bool ensure_pinned(Flight &f, size_t bytes)
 // requests are owned by this launch until completion.
 int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &rq)
 {
+    NvtxScope range("aidw serving flight");
     aidw_ctx *ctx = rt->ctx;
     cudaStream_t st = f.stream;
     // Staging sizes.
