@@ -120,6 +120,26 @@ void finish(ServingRuntime *rt, const std::vector<int64_t> &ids, int status)
     }
 }
 
+// Admission of the request at the head of the queue into the flight being assembled (pure host
+// logic; aidw_debug_admission runs it without a GPU). Requests are taken in arrival order: a
+// request that does not fit stops the flight (no overtaking), a request that could never fit
+// the budget fails with OOM, and FP64 / kNN-output requests run alone.
+enum class Admit { kTake, kSolo, kRejectOom, kStop };
+
+Admit admission_step(bool solo, size_t footprint, size_t budget, size_t in_flight,
+                     size_t flight_bytes, size_t flight_count, int max_items)
+{
+    if (static_cast<int64_t>(flight_count) >= max_items)
+        return Admit::kStop;
+    if (solo)
+        return flight_count == 0 ? Admit::kSolo : Admit::kStop;
+    if (footprint > budget)
+        return Admit::kRejectOom;
+    if (in_flight + flight_bytes + footprint > budget)
+        return Admit::kStop;
+    return Admit::kTake;
+}
+
 bool ensure_pinned(Flight &f, size_t bytes)
 {
     if (f.pinned_bytes >= bytes)
@@ -271,12 +291,14 @@ void worker_main(ServingRuntime *rt)
             std::vector<int64_t> ids;
             std::vector<Request *> rq;
             size_t fp = 0;
-            while (!rt->queue.empty() && static_cast<int>(ids.size()) < rt->max_items) {
+            while (!rt->queue.empty()) {
                 const int64_t id = rt->queue.front();
                 Request &r = rt->reqs[id];
-                if (r.solo) {
-                    if (!ids.empty())
-                        break;  // runs alone, next round
+                const Admit a = admission_step(r.solo, r.footprint, rt->budget, rt->in_flight, fp,
+                                               ids.size(), rt->max_items);
+                if (a == Admit::kStop)
+                    break;  // the head waits for the next flight or for memory to free up
+                if (a == Admit::kSolo) {
                     rt->queue.pop_front();
                     g.unlock();
                     int rc = interpolate_impl(rt->ctx, r.ds, r.qx, r.qy, r.m, &r.p, r.out,
@@ -289,14 +311,12 @@ void worker_main(ServingRuntime *rt)
                     rt->cv_done.notify_all();
                     continue;
                 }
-                if (r.footprint > rt->budget) {
+                if (a == Admit::kRejectOom) {
                     rt->queue.pop_front();
                     finish(rt, {id}, AIDW_ERR_OOM);
                     rt->cv_done.notify_all();
                     continue;
                 }
-                if (rt->in_flight + fp + r.footprint > rt->budget)
-                    break;  // admitted when memory frees up
                 rt->queue.pop_front();
                 ids.push_back(id);
                 rq.push_back(&r);
@@ -392,6 +412,44 @@ void serving_stop(ServingRuntime *rt)
 using namespace aidw;
 
 extern "C" {
+
+// Test hook (not in the public header): runs the serving runtime's admission of one flight over
+// a queue of `count` requests (solo flags, device footprints) against `budget` with `in_flight`
+// bytes already running, and writes each request's action: 0 taken into the flight, 1 run alone,
+// 2 failed with OOM, 3 left in the queue. Host only.
+int aidw_debug_admission(int64_t count, const int32_t *solo, const uint64_t *footprint,
+                         uint64_t budget, uint64_t in_flight, int32_t max_items, int32_t *action)
+{
+    if (count < 0 || max_items < 1 || (count > 0 && (!solo || !footprint || !action)))
+        return AIDW_ERR_INVALID_ARG;
+    size_t fp = 0, n = 0;
+    bool stopped = false;
+    for (int64_t i = 0; i < count; ++i) {
+        if (stopped) {
+            action[i] = 3;
+            continue;
+        }
+        switch (admission_step(solo[i] != 0, footprint[i], budget, in_flight, fp, n,
+                               max_items)) {
+        case Admit::kTake:
+            action[i] = 0;
+            fp += footprint[i];
+            ++n;
+            break;
+        case Admit::kSolo:
+            action[i] = 1;
+            break;
+        case Admit::kRejectOom:
+            action[i] = 2;
+            break;
+        case Admit::kStop:
+            action[i] = 3;
+            stopped = true;
+            break;
+        }
+    }
+    return AIDW_OK;
+}
 
 int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_batch_requests,
                            int32_t streams)
