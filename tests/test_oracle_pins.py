@@ -122,6 +122,24 @@ def pin_failures(lib=None, quick=False):
             fails.append(f"{c['name']}: Z {r['z'][0]}")
         if r["knn"].tolist() != c["knn"]:
             fails.append(f"{c['name']}: knn {r['knn'].tolist()}")
+        if not math.isclose(r["scale"][0], closed(c["scale"]), rel_tol=1e-14):
+            fails.append(f"{c['name']}: S* {r['scale'][0]}")
+
+    # S* = sum(w|z|)/sum(w) is the weighted mean of |z| under the same weights: it equals Z
+    # for z >= 0, equals the Z of |z| for any z, and ignores the sign of z.
+    wl = workloads.small_case(17, 300, 40, pattern="clustered")
+    zs = wl.z - np.median(wl.z)  # both signs
+    for zz in (np.abs(zs) + 0.5, zs):
+        r = oracle.interpolate(wl.x, wl.y, zz, wl.area, wl.qx, wl.qy, wl.k, threads=1, lib=lib)
+        ra = oracle.interpolate(wl.x, wl.y, np.abs(zz), wl.area, wl.qx, wl.qy, wl.k, threads=1,
+                                lib=lib)
+        rn = oracle.interpolate(wl.x, wl.y, -zz, wl.area, wl.qx, wl.qy, wl.k, threads=1, lib=lib)
+        if not np.allclose(r["scale"], ra["z"], rtol=1e-15, atol=0):
+            fails.append("S* differs from the weighted mean of |z|")
+        if not (np.array_equal(rn["scale"], r["scale"]) and np.array_equal(rn["z"], -r["z"])):
+            fails.append("S* or Z not odd/even under z -> -z")
+        if np.all(zz >= 0) and not np.allclose(r["scale"], r["z"], rtol=1e-15, atol=0):
+            fails.append("S* differs from Z for z >= 0")
 
     for seed in range(2 if quick else 4):
         x, y, qx, qy = lattice_case(seed)
@@ -273,6 +291,12 @@ MUTANTS = {
                             "for (int64_t i = 0; i < w->k; ++i) {\n            double dd"),
     "dist_transposed": ("return dx * dx + dy * dy;", "return dx * dx + dx * dy;"),
     "coincident_first_only": ("Z = (sz0 + cz0) / (double)n0;", "Z = (sz0 + cz0);"),
+    "scale_not_normalised": ("scale = (swa + cwa) / W;", "scale = (swa + cwa);"),
+    "scale_signed": ("neumaier_add(&swa, &cwa, wi * fabs(w->z[i]));",
+                     "neumaier_add(&swa, &cwa, wi * w->z[i]);"),
+    "scale_coincident_sum": ("scale = (sa0 + ca0) / (double)n0;", "scale = (sa0 + ca0);"),
+    "scale_coincident_signed": ("neumaier_add(&sa0, &ca0, fabs(w->z[i]));",
+                                "neumaier_add(&sa0, &ca0, w->z[i]);"),
 }
 
 
