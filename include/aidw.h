@@ -89,6 +89,8 @@ void aidw_params_default(aidw_params *p);
 /* ---- context -------------------------------------------------------------------------- */
 /* Creates a context on CUDA device `device`. hbm_budget_bytes caps the device memory the
  * context holds at once (datasets + per-call scratch); 0 means "whatever the device has".
+ * It also places aidw_interpolate_noalloc's 16 MiB scratch array on the device (once per
+ * device and process; not charged to the budget).
  * Returns AIDW_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
 int aidw_init(aidw_ctx **out, int device, size_t hbm_budget_bytes);
 
@@ -141,15 +143,25 @@ int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int
  * device synchronisation of cudaFree: this call performs no cudaMalloc, cudaFree or other
  * allocation. Its scratch is one 16 MiB __device__ array inside the library, held on every
  * GPU that loads the library until the process exits. The context and the dataset are
- * created beforehand (they allocate once, at set-up).
+ * created beforehand (they allocate once, at set-up); aidw_init also places the array on the
+ * context's device and looks up its address, so that under CUDA's lazy module loading the
+ * array is committed at set-up and not by a call. Kernel code is a separate matter: under lazy
+ * module loading the CUDA driver loads a kernel at its first launch, so a caller that may not
+ * allocate at all after set-up makes one call of each size class it will serve during set-up
+ * (or runs with CUDA_MODULE_LOADING=EAGER).
  *   qx, qy, out  DEVICE arrays of m floats on the context's device (host arrays are rejected)
  *   p            as for aidw_interpolate; p->precision must be AIDW_F32C
- * Limit: about m * (4k + 24) bytes must fit in 16 MiB (m <= 262,144 for k = 10, about
- * 110,000 for k = 32); larger calls return AIDW_ERR_INVALID_ARG. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress), so make that first call before
- * any stream capture. All calls share the one array: calls whose work overlaps on the GPU (for
- * example on two streams) race and must be serialised by the caller. Stream-ordered on `stream`;
- * kernel timeouts are reported by aidw_check_device_errors. */
+ * Phase 1 takes aidw_interpolate's pruned route (queries put in Z-order, nearest data tiles
+ * first) when aidw_interpolate would and its scratch, about m * (4k + 49) bytes, fits the array
+ * (m up to about 189,000 at k = 10); otherwise it scans every (query, data point) pair in data
+ * splits, which for many queries costs far more (at 131,072 queries x 1M points about 61 ms
+ * against 3.4 ms for the pruned scan; phase 2 is the same either way). Limit: the split scan
+ * needs about m * (4k + 24) bytes within 16 MiB (m <= 262,144 for k = 10, about 110,000 for
+ * k = 32); larger calls return AIDW_ERR_INVALID_ARG. All calls share the one array and it keeps
+ * the last call's contents (every element a call reads, it has written first): calls whose
+ * work overlaps on the GPU (for example on two streams) race and must be serialised by the
+ * caller. Stream-ordered on `stream`; kernel timeouts are reported by
+ * aidw_check_device_errors. */
 int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, const float *qy,
                              int64_t m, const aidw_params *p, float *out, void *stream);
 

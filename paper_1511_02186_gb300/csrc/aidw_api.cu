@@ -183,20 +183,26 @@ int ctx_sm_count(aidw_ctx *ctx)
     return ctx->sm_count;
 }
 
-const DatasetRec *ctx_dataset(aidw_ctx *ctx, aidw_dataset id)
+// Copies a dataset's record while holding the context lock, so that a concurrent
+// aidw_destroy_dataset (which erases the record under the same lock) cannot free it while it is
+// read; no pointer into the table leaves the lock.
+static bool ctx_dataset_copy(aidw_ctx *ctx, aidw_dataset id, DatasetRec *out)
 {
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->datasets.find(id);
-    return it == ctx->datasets.end() ? nullptr : &it->second;
+    if (it == ctx->datasets.end())
+        return false;
+    *out = it->second;
+    return true;
 }
 
 bool dataset_lookup(aidw_ctx *ctx, aidw_dataset id, DatasetDev *dev, double *r_exp)
 {
-    const DatasetRec *r = ctx_dataset(ctx, id);
-    if (!r)
+    DatasetRec r;
+    if (!ctx_dataset_copy(ctx, id, &r))
         return false;
-    *dev = r->dev;
-    *r_exp = r->r_exp;
+    *dev = r.dev;
+    *r_exp = r.r_exp;
     return true;
 }
 
@@ -483,6 +489,14 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
            static_cast<double>(m) >= need;
 }
 
+void plan_culled_knn(Plan *pl, int64_t n_pad)
+{
+    pl->knn.splits = 1;
+    pl->knn.split_len = n_pad;
+    pl->knn.q_per_block = kThreads * pl->kq;
+    pl->knn.qblocks = static_cast<int>((pl->m + pl->knn.q_per_block - 1) / pl->knn.q_per_block);
+}
+
 size_t culled_extra_bytes(int64_t m, int precision)
 {
     const size_t mm = static_cast<size_t>(m);
@@ -624,12 +638,8 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
                         force_knn_splits, force_w_splits, cfg);
     const bool cull =
         force_knn_splits == 0 && use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl);
-    if (cull) {
-        pl.knn.splits = 1;
-        pl.knn.split_len = ds.n_pad;
-        pl.knn.q_per_block = kThreads * pl.kq;
-        pl.knn.qblocks = static_cast<int>((m + pl.knn.q_per_block - 1) / pl.knn.q_per_block);
-    }
+    if (cull)
+        plan_culled_knn(&pl, ds.n_pad);
     const size_t sb = scratch_bytes(p->precision, pl, p->k) +
                       (cull ? culled_extra_bytes(m, p->precision) : 0);
     // Staging for host arrays.
@@ -774,6 +784,9 @@ int aidw_init(aidw_ctx **out, int device, size_t hbm_budget_bytes)
     ok = ok && cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess;
     for (int i = 0; ok && i < 5; ++i)
         ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    // Places aidw_interpolate_noalloc's fixed scratch array on the device now, at set-up, so
+    // that its calls never load a module (and its 16 MiB) in the middle of a request.
+    ok = ok && noalloc_prepare(device) == AIDW_OK;
     if (!ok) {
         cudaGetLastError();
         aidw_shutdown(ctx);
@@ -1008,13 +1021,13 @@ int aidw_dataset_info(aidw_ctx *ctx, aidw_dataset ds, int64_t *n, size_t *device
 {
     if (!ctx)
         return AIDW_ERR_INVALID_ARG;
-    const DatasetRec *r = ctx_dataset(ctx, ds);
-    if (!r)
+    DatasetRec r;
+    if (!ctx_dataset_copy(ctx, ds, &r))
         return AIDW_ERR_NOT_FOUND;
     if (n)
-        *n = r->dev.n;
+        *n = r.dev.n;
     if (device_bytes)
-        *device_bytes = r->bytes;
+        *device_bytes = r.bytes;
     return AIDW_OK;
 }
 

@@ -60,6 +60,20 @@ int enqueue_interpolation(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, con
                           const aidw_params &p, const void *qx, const void *qy,
                           const Scratch &sc, void *out, float *out_alpha, int32_t *out_knn,
                           cudaStream_t st, bool profile);
+// The pruned phase 1 (Z-ordered queries, nearest tiles first): whether a call takes it, the
+// plan change it needs (one query block per CTA, no data splits), the scratch it needs beyond
+// scratch_bytes (query ordering), and the enqueue.
+bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_idx,
+                    const Plan &pl);
+void plan_culled_knn(Plan *pl, int64_t n_pad);
+size_t culled_extra_bytes(int64_t m, int precision);
+int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
+                   const aidw_params &p, const void *qx, const void *qy, const Scratch &sc,
+                   void *extra, void *out, float *out_alpha, int32_t *out_knn, cudaStream_t st,
+                   bool profile);
+// Resolves the device address of aidw_interpolate_noalloc's scratch array on `device` (made
+// current by the caller); called once per context at aidw_init.
+int noalloc_prepare(int device);
 
 // Stops the serving thread (waits for admitted work) and frees its state; null is a no-op.
 void serving_stop(ServingRuntime *rt);

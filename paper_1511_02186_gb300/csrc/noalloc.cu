@@ -10,8 +10,15 @@
 // The scratch area is a file-scope __device__ array of kNoAllocScratchBytes. Every GPU that
 // loads the library holds it until the process exits. Host code cannot use the array's name
 // as a device address (in host code it names a host-side stand-in), so the device address is
-// looked up with cudaGetSymbolAddress once per device, on the first call made on that device,
-// with that device current; that first call should therefore come before any stream capture.
+// looked up with cudaGetSymbolAddress once per device, with that device current. aidw_init does
+// this when it creates a context: under CUDA's lazy module loading the lookup is what places
+// this file's module, and with it the array, on the device, so it belongs at set-up and not in
+// the middle of a request.
+//
+// The call takes the same phase-1 route as aidw_interpolate when its scratch fits: with enough
+// queries, the pruned scan over Z-ordered queries (the query ordering needs about 24 more bytes
+// per query); otherwise, or when that does not fit, the split scan with as few splits as the
+// area requires.
 #include <mutex>
 
 #include "aidw_internal.cuh"
@@ -46,6 +53,12 @@ void *scratch_address(int device)
 }
 
 }  // namespace
+
+int noalloc_prepare(int device)
+{
+    return scratch_address(device) ? AIDW_OK : AIDW_ERR_CUDA;
+}
+
 }  // namespace aidw
 
 using namespace aidw;
@@ -73,11 +86,37 @@ extern "C" int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const fl
         return AIDW_ERR_INVALID_ARG;  // device arrays only: host arrays would need staging
     if (cudaSetDevice(device) != cudaSuccess)
         return AIDW_ERR_CUDA;
-    void *base = scratch_address(device);
+    void *base = scratch_address(device);  // resolved by aidw_init: a table read here
     if (!base)
         return AIDW_ERR_CUDA;
-    // Plan as usual, then give up splits until the scratch fits the fixed area.
-    Plan pl = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, 0);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Plan planned = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, 0);
+
+    // Pruned phase 1 where aidw_interpolate would take it, with fewer phase-2 splits if the
+    // area needs it (splits only regroup the FP32 partial sums).
+    if (use_culled_knn(AIDW_F32C, dev, m, false, planned)) {
+        Plan pl = planned;
+        plan_culled_knn(&pl, dev.n_pad);
+        const size_t extra = culled_extra_bytes(m, AIDW_F32C);
+        while (scratch_bytes(AIDW_F32C, pl, p->k) + extra > kNoAllocScratchBytes &&
+               pl.w.splits > 1) {
+            pl = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, pl.w.splits - 1);
+            plan_culled_knn(&pl, dev.n_pad);
+        }
+        const size_t sb = scratch_bytes(AIDW_F32C, pl, p->k);
+        if (sb + extra <= kNoAllocScratchBytes) {
+            Scratch sc;
+            scratch_carve(base, AIDW_F32C, pl, p->k, &sc);
+            // Every scratch element (lists, parameters, partial sums, sort keys and counts,
+            // ordered queries) is written before it is read, so nothing needs clearing.
+            return enqueue_culled(ctx, dev, r_exp, pl, *p, qx, qy, sc,
+                                  static_cast<char *>(base) + sb, out, nullptr, nullptr, st,
+                                  false);
+        }
+    }
+
+    // Split scan: plan as usual, then give up splits until the scratch fits the fixed area.
+    Plan pl = planned;
     while (scratch_bytes(AIDW_F32C, pl, p->k) > kNoAllocScratchBytes &&
            (pl.knn.splits > 1 || pl.w.splits > 1)) {
         const int s1 = pl.knn.splits > 1 ? pl.knn.splits - 1 : 1;
@@ -89,6 +128,6 @@ extern "C" int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const fl
     Scratch sc;
     scratch_carve(base, AIDW_F32C, pl, p->k, &sc);
     // Every scratch element is written before it is read, so nothing needs clearing.
-    return enqueue_interpolation(ctx, dev, r_exp, pl, *p, qx, qy, sc, out, nullptr, nullptr,
-                                 static_cast<cudaStream_t>(stream), false);
+    return enqueue_interpolation(ctx, dev, r_exp, pl, *p, qx, qy, sc, out, nullptr, nullptr, st,
+                                 false);
 }

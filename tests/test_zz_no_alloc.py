@@ -28,33 +28,73 @@ def _noalloc(ctx, ds, qx, qy, params, out):
     return rc
 
 
+def _check_against_interpolate(ctx, wl):
+    """One call of each entry point on the same device arrays; predictions within the FP32
+    tolerance, relative to max(|Z|, sum w|z| / sum w) (z changes sign)."""
+    import torch
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx = torch.as_tensor(wl.qx, dtype=torch.float32, device="cuda")
+    qy = torch.as_tensor(wl.qy, dtype=torch.float32, device="cuda")
+    p = aidw.default_params(k=wl.k, levels=wl.levels)
+    ref, _, _ = ctx.interpolate(ds, qx, qy, p)
+    # Condition scale of each prediction, from the same weights: the denominator the parity
+    # tests use.
+    ds_abs = ctx.create_dataset(wl.x, wl.y, np.abs(wl.z), wl.area)
+    scale_t, _, _ = ctx.interpolate(ds_abs, qx, qy, p)
+    out = torch.full((wl.m,), float("nan"), dtype=torch.float32, device="cuda")
+    assert _noalloc(ctx, ds, qx, qy, p, out) == aidw.OK
+    torch.cuda.synchronize()
+    assert ctx.check_device_errors() == aidw.OK
+    a = out.cpu().numpy().astype(np.float64)
+    b = ref.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a))
+    scale = np.maximum(np.abs(b), scale_t.cpu().numpy().astype(np.float64))
+    assert (np.abs(a - b) / scale).max() <= TOL_F32
+    ds.destroy()
+    ds_abs.destroy()
+
+
 def test_noalloc_matches_interpolate_twice():
+    """Two calls in a row on the pruned phase-1 route (enough queries, scratch fits), different
+    sizes, the same scratch array."""
     import torch
     assert torch.cuda.is_available()
     with aidw.Context(0) as ctx:
-        runs = [workloads.small_case(201, 40000, 30000, k=10, pattern="clustered"),
-                workloads.small_case(202, 25000, 50000, k=15, pattern="uniform")]
-        for wl in runs:  # two calls in a row, different sizes, same scratch array
-            ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
-            qx = torch.as_tensor(wl.qx, dtype=torch.float32, device="cuda")
-            qy = torch.as_tensor(wl.qy, dtype=torch.float32, device="cuda")
-            p = aidw.default_params(k=wl.k, levels=wl.levels)
-            ref, _, _ = ctx.interpolate(ds, qx, qy, p)
-            # Condition scale sum(w|z|)/sum(w) of each prediction, from the same weights: the
-            # denominator the parity tests use, since z changes sign.
-            ds_abs = ctx.create_dataset(wl.x, wl.y, np.abs(wl.z), wl.area)
-            scale_t, _, _ = ctx.interpolate(ds_abs, qx, qy, p)
-            out = torch.full((wl.m,), float("nan"), dtype=torch.float32, device="cuda")
+        for wl in (workloads.small_case(201, 40000, 30000, k=10, pattern="clustered"),
+                   workloads.small_case(202, 25000, 50000, k=15, pattern="uniform")):
+            _check_against_interpolate(ctx, wl)
+
+
+def test_noalloc_split_scan_routes():
+    """Few queries (split scan, as aidw_interpolate) and more queries than the pruned route's
+    scratch allows at k = 10 (split scan with fewer splits)."""
+    with aidw.Context(0) as ctx:
+        for wl in (workloads.small_case(204, 30000, 3000, k=10, pattern="clustered"),
+                   workloads.small_case(205, 6000, 230000, k=10, pattern="uniform")):
+            _check_against_interpolate(ctx, wl)
+
+
+def test_noalloc_call_allocates_nothing():
+    """After a first call of the same size (under lazy module loading the driver loads kernel
+    code at a kernel's first launch), further calls leave the device's free memory unchanged."""
+    import torch
+    with aidw.Context(0) as ctx:
+        wl = workloads.small_case(206, 20000, 40000, k=10, pattern="clustered")
+        ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+        qx = torch.as_tensor(wl.qx, dtype=torch.float32, device="cuda")
+        qy = torch.as_tensor(wl.qy, dtype=torch.float32, device="cuda")
+        out = torch.empty(wl.m, dtype=torch.float32, device="cuda")
+        p = aidw.default_params(k=10)
+        assert _noalloc(ctx, ds, qx, qy, p, out) == aidw.OK
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(3):
             assert _noalloc(ctx, ds, qx, qy, p, out) == aidw.OK
-            torch.cuda.synchronize()
-            assert ctx.check_device_errors() == aidw.OK
-            a = out.cpu().numpy().astype(np.float64)
-            b = ref.cpu().numpy().astype(np.float64)
-            assert np.all(np.isfinite(a))
-            scale = np.maximum(np.abs(b), scale_t.cpu().numpy().astype(np.float64))
-            assert (np.abs(a - b) / scale).max() <= TOL_F32
-            ds.destroy()
-            ds_abs.destroy()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+        assert ctx.check_device_errors() == aidw.OK
+        ds.destroy()
 
 
 def test_noalloc_rejects_what_it_cannot_do():
