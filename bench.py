@@ -6,10 +6,12 @@ R_min = 0, R_max = 2 -- the paper's largest size class (Sec. 4: as many queries 
 uniform in a square), seeded synthetic data. A pair-evaluation is one (query, data point) pair
 carried through both phases (kNN scan and weighted sum); a step is n * m of them.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Prints one JSON line (rank 0). Under torchrun every rank runs its own full-size problem (query
-sets are independent; no collective on the data path) and the value is all ranks' pairs over
-the slowest rank's time.
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--scaling S]
+Prints one JSON line (rank 0). Under torchrun the queries are sharded over the ranks, each rank
+holding a replica of the dataset on its own GPU (queries are independent; no collective on the
+data path): with --scaling weak (the default) every rank interpolates its own 1,048,576
+queries, with --scaling strong the workload's queries are split into contiguous ranges. The
+value is all ranks' pair-evaluations over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -81,6 +83,25 @@ def workload_config(wl):
             "levels": list(wl.levels), "r_min": wl.r_min, "r_max": wl.r_max, "area": wl.area,
             "domain": "[0,1000]^2", "seed": 0,
             "l2": "flushed between timed steps by a 256 MiB write (outside the timed events)"}
+
+
+def rank_workload(wl, rank: int, world: int, scaling: str):
+    """This rank's queries against the replicated dataset. Strong scaling: its contiguous range
+    of the workload's queries (query_ranges). Weak scaling: a full query set of its own (rank 0
+    the workload's, rank r > 0 fresh seeded uniform points in the same square), so that every
+    rank does the same amount of work as N grows."""
+    import dataclasses
+    from paper_1511_02186_gb300.sharding import query_ranges
+    if world == 1:
+        return wl
+    if scaling == "strong":
+        b, e = query_ranges(wl.m, world)[rank]
+        return wl.query_subset(np.arange(b, e))
+    if rank == 0:
+        return wl
+    rng = np.random.default_rng(1000 + rank)
+    side = float(np.sqrt(wl.area))
+    return dataclasses.replace(wl, qx=rng.uniform(0.0, side, wl.m), qy=rng.uniform(0.0, side, wl.m))
 
 
 # ---- clocks ------------------------------------------------------------------------------
@@ -235,11 +256,11 @@ def oracle_rate_small(wl, threads):
 
 # ---- batched and served configurations -------------------------------------------------------
 
-def bench_batched(ctx, steps: int, warmup: int, dev, stream):
+def bench_batched(ctx, steps: int, warmup: int, dev, stream, tune: bool = True):
     """256 independent datasets (n log-uniform in [1,024, 262,144], m log-uniform in
     [1,024, 65,536], side log-uniform in [10, 1000], uniform or clustered, k in {6, 10, 15}) in
     one persistent launch replayed from a CUDA graph: timed with the built-in kernel shape,
-    then autotuned on the batch itself and timed again with the winning shape."""
+    then (with `tune`) autotuned on the batch itself and timed again with the winning shape."""
     import torch
     from paper_1511_02186_gb300 import aidw, workloads
     wls = workloads.batched(0)
@@ -268,9 +289,12 @@ def bench_batched(ctx, steps: int, warmup: int, dev, stream):
 
     ms_default = timed()
     t0 = time.perf_counter()
-    cfg, tune_ms = pb.autotune(reps=2)
+    if tune:
+        cfg, tune_ms = pb.autotune(reps=2)
+        ms = timed()
+    else:
+        cfg, ms = pb.config(), ms_default
     tune_s = time.perf_counter() - t0
-    ms = timed()
     pb.destroy()
     for it in items:
         it[0].destroy()
@@ -312,60 +336,100 @@ def bench_standard_idw(ctx, ds, wl, dev, stream, peak):
             "ms": ms, "value": value, "unit": UNIT, "frac_of_phase2_bound": value / peak}
 
 
-def bench_served(ctx, capacity_pairs_s: float, window_s: float, nominal_window_s: float):
+SERVED_BUCKETS = ((256, 4096), (4096, 65536), (65536, 262145))
+
+
+def latency_summary(lat_ms, ms_):
+    """p50 / p99 / max of request latencies, overall and per query-count bucket."""
+    lat_ms, ms_ = np.asarray(lat_ms), np.asarray(ms_)
+    out = {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+           "max_ms": float(lat_ms.max())}
+    by = {}
+    for lo, hi in SERVED_BUCKETS:
+        sel = (ms_ >= lo) & (ms_ < hi)
+        if sel.any():
+            by[f"{lo}-{hi - 1}_queries"] = {
+                "requests": int(sel.sum()), "p50_ms": float(np.percentile(lat_ms[sel], 50)),
+                "p99_ms": float(np.percentile(lat_ms[sel], 99))}
+    out["by_request_size"] = by
+    return out
+
+
+def bench_served(ctx, capacity_pairs_s: float, requests_per_level: int, nominal_window_s: float,
+                 nominal_queue: int):
     """64 resident datasets (n log-uniform in [16K, 1M]); Poisson arrivals of requests with
     256..262,144 query points (log-uniform, host arrays) uniform in the dataset's square.
-    Runs at 0.25, 0.5 and 0.8 of the measured single-launch capacity and at the nominal
-    2,000 req/s (an offered load several times the capacity: admission and backpressure),
-    then serves a prefix of the same request stream one request per launch (FP64 and FP32,
-    no batching) for comparison."""
+    Runs at 0.25, 0.5 and 0.8 of the measured single-launch capacity (about
+    `requests_per_level` requests each; a refused submit is retried after 1 ms) and at the
+    nominal 2,000 req/s over `nominal_window_s` seconds, an offered load several times the
+    capacity, against a serving queue of `nominal_queue` requests: a submit refused with
+    AIDW_ERR_AGAIN is shed (counted, not retried), which is the backpressure a client sees.
+    Latencies are reported overall and per request-size bucket. Then serves a prefix of a
+    request stream one request per launch (FP64 and FP32, no batching) for comparison."""
     from paper_1511_02186_gb300 import aidw, workloads
     dsw = workloads.served_datasets(0)
     handles = [ctx.create_dataset(w.x, w.y, w.z, w.area) for w in dsw]
+    pool = workloads.served_query_pool(dsw)
     p = aidw.default_params(k=10)
-    probe = workloads.served_requests(dsw, seed=11, rate=2000.0, duration_s=1.0)
-    mean_pairs = statistics.mean(dsw[d].n * len(qx) for _, d, qx, _ in probe)
-    results = {"mean_pair_evals_per_request": mean_pairs}
-    runs = [(f"load_{f:.2f}_of_capacity", max(1.0, f * capacity_pairs_s / mean_pairs), window_s,
-             12 + i) for i, f in enumerate((0.25, 0.5, 0.8))]
-    runs.append(("nominal_2000_per_s", 2000.0, nominal_window_s, 20))
-    for label, rate, window, seed in runs:
-        reqs = workloads.served_requests(dsw, seed=seed, rate=rate, duration_s=window)
-        prepared = [(t, d, qx.astype(np.float32), qy.astype(np.float32),
-                     np.empty(len(qx), dtype=np.float32)) for t, d, qx, qy in reqs]
+    probe = workloads.served_arrivals(dsw, seed=11, rate=2000.0, duration_s=1.0)
+    mean_pairs = statistics.mean(dsw[d].n * m for _, d, m in probe)
+    results = {"mean_pair_evals_per_request": mean_pairs,
+               "queries": "slices of a per-dataset pool of 262,144 seeded uniform points"}
+    runs = []
+    for i, f in enumerate((0.25, 0.5, 0.8)):
+        rate = max(1.0, f * capacity_pairs_s / mean_pairs)
+        runs.append((f"load_{f:.2f}_of_capacity", rate, requests_per_level / rate, 12 + i, 0))
+    runs.append(("nominal_2000_per_s", 2000.0, nominal_window_s, 20, nominal_queue))
+    rng = np.random.default_rng(21)
+    for label, rate, window, seed, queue in runs:
+        arrivals = workloads.served_arrivals(dsw, seed=seed, rate=rate, duration_s=window)
+        if queue:
+            ctx.serving_set_queue_limit(queue)
         ids = []
-        again = 0
+        again = shed = 0
         t0 = time.perf_counter()
-        for t, d, qx, qy, out in prepared:
+        for t, d, m in arrivals:
             now = time.perf_counter() - t0
             if t > now:
                 time.sleep(t - now)
+            off = int(rng.integers(0, len(pool[d][0]) - m + 1))
+            qx, qy = pool[d][0][off:off + m], pool[d][1][off:off + m]
+            out = np.empty(m, dtype=np.float32)
             while True:
                 rc, rid = ctx.submit(handles[d], qx, qy, p, out)
-                if rc == aidw.ERR_AGAIN:
-                    again += 1
-                    time.sleep(0.001)
-                    continue
-                break
-            ids.append((rid, dsw[d].n * len(qx)))
-        for rid, _ in ids:
+                if rc != aidw.ERR_AGAIN:
+                    break
+                again += 1
+                if queue:
+                    break  # shed
+                time.sleep(0.001)
+            if rc == aidw.ERR_AGAIN:
+                shed += 1
+                continue
+            ids.append((rid, dsw[d].n * m, m))
+        t_submitted = time.perf_counter() - t0
+        for rid, _, _ in ids:
             ctx.wait(rid, -1)
         wall = time.perf_counter() - t0
-        lat = np.array([ctx.latency_us(rid) for rid, _ in ids]) / 1e3
-        for rid, _ in ids:
+        lat = np.array([ctx.latency_us(rid) for rid, _, _ in ids]) / 1e3
+        for rid, _, _ in ids:
             ctx.release(rid)
-        pairs = float(sum(x for _, x in ids))
-        results[label] = {"rate_req_per_s": rate, "window_s": window, "requests": len(ids),
-                          "p50_ms": float(np.percentile(lat, 50)),
-                          "p99_ms": float(np.percentile(lat, 99)),
-                          "max_ms": float(lat.max()),
+        if queue:
+            ctx.serving_set_queue_limit(4096)
+        pairs = float(sum(x for _, x, _ in ids))
+        results[label] = {"rate_req_per_s": rate, "window_s": window, "offered_requests":
+                          len(arrivals), "requests": len(ids),
+                          **latency_summary(lat, [m for _, _, m in ids]),
                           "throughput": pairs / wall, "unit": UNIT,
-                          "offered": rate * mean_pairs, "resubmits_after_again": again}
+                          "offered": rate * mean_pairs, "refused_again": again,
+                          "shed": shed, "queue_limit": queue or 4096,
+                          "submit_phase_s": t_submitted, "wall_s": wall}
     results["sustained"] = results["load_0.50_of_capacity"]
     st = ctx.serving_stats()
     results["launches"] = int(st.launches)
     results["max_concurrent_launches"] = int(st.max_concurrent_launches)
     results["mean_requests_per_launch"] = st.batched_requests / max(1, st.launches)
+    results["rejected_again_total"] = int(st.rejected_again)
     results["workload"] = "served_64_datasets_poisson"
 
     # One set of requests served three ways with nothing else running: one synchronous call per
@@ -538,6 +602,22 @@ def bench_precision_stress(ctx, dev, stream):
 
 # ---- GPU arm -----------------------------------------------------------------------------------
 
+def run_batched_leg(args):
+    """The batched workload alone (profiling runs of the batch kernel): one JSON line."""
+    import torch
+    from paper_1511_02186_gb300 import aidw
+    import __graft_entry__
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    with aidw.Context(0) as ctx:
+        r = bench_batched(ctx, args.steps, args.warmup, dev, torch.cuda.current_stream(dev),
+                          tune=args.extras)
+    r["note"] = "batched leg alone" + ("" if args.extras else ", built-in kernel shape")
+    print(json.dumps(r), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
     from paper_1511_02186_gb300 import aidw, workloads
@@ -546,7 +626,11 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     __graft_entry__.build()
-    wl = workloads.uniform_paper(0, n=args.n, m=args.m or args.n)
+    job_wl = workloads.uniform_paper(0, n=args.n, m=args.m or args.n)
+    wl = rank_workload(job_wl, rank, world, args.scaling)
+    # Pair-evaluations of the whole job (all ranks) per step.
+    job_pairs = float(job_wl.n) * job_wl.m * (world if args.scaling == "weak" else 1)
+    job_queries = job_wl.m * (world if args.scaling == "weak" else 1)
     ctx = aidw.Context(local)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
     f64 = args.precision in ("f64", "f64x")
@@ -593,8 +677,8 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     total_s = max_over_ranks(total_s, world, dev)
-    pairs = float(wl.n) * wl.m
-    value = world * pairs * args.steps / total_s
+    pairs = float(wl.n) * wl.m  # this rank's
+    value = job_pairs * args.steps / total_s
 
     # Roofline of the dominant kernel (largest device time per step).
     kn = statistics.mean(t.knn_ms for t in ktimes)
@@ -695,7 +779,7 @@ def run_gpu(args):
         ctx.interpolate(d2, hqx, hqy, p, out=hout, stream=stream.cuda_stream)
         d2.destroy()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_val = world * pairs * e2e_steps / e2e_s
+    e2e_val = job_pairs * e2e_steps / e2e_s
     h2d = 3 * 8 * wl.n + 2 * 4 * wl.m
     d2h = 4 * wl.m
 
@@ -709,7 +793,8 @@ def run_gpu(args):
         # The serving runtime batches many small requests like the batched workload: it runs
         # with the kernel shape the autotuner picked there.
         sctx.set_tune_config(aidw.tune_config(**batched["tuned_config"]))
-        served = bench_served(sctx, value / world, 2.0, args.nominal_window)
+        served = bench_served(sctx, value / world, args.served_requests, args.nominal_window,
+                              args.nominal_queue)
         served["kernel_shape"] = batched["tuned_config"]
         sctx.close()
 
@@ -727,10 +812,15 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": args.scaling, "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded uniform points in [0,1000]^2, n = m = 1,048,576)",
-            "config": workload_config(wl),
-            "queries_per_s": world * wl.m * args.steps / total_s,
+            "config": dict(workload_config(job_wl), parallelism=(
+                "single GPU" if world == 1 else
+                f"query sharding over {world} ranks, dataset replicated, no collective on the "
+                f"data path ({args.scaling} scaling: " +
+                ("each rank its own 1,048,576 queries)" if args.scaling == "weak" else
+                 "the workload's queries split into contiguous ranges)"))),
+            "queries_per_s": job_queries * args.steps / total_s,
             "kernel_ms": {"knn_incl_query_ordering": kn, "select": ks, "weights": kw,
                           "finalize": kf},
             "plan": {"knn_splits": ktimes[0].splits, "w_splits": ktimes[0].weight_splits,
@@ -840,10 +930,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=N_DATA,
                     help="data and query count (smaller sizes only for profiling runs)")
-    ap.add_argument("--nominal-window", type=float, default=0.5,
-                    help="arrival window (s) of the served run at the nominal 2,000 req/s; its "
-                         "offered load is several times the capacity, so the run lasts about "
-                         "8 s per second of window")
+    ap.add_argument("--nominal-window", type=float, default=10.0,
+                    help="arrival window (s) of the served run at the nominal 2,000 req/s (an "
+                         "offered load several times the capacity; refused requests are shed)")
+    ap.add_argument("--nominal-queue", type=int, default=64,
+                    help="serving queue length during the nominal-rate run")
+    ap.add_argument("--served-requests", type=int, default=1000,
+                    help="requests offered at each sub-capacity load level of the served run")
     ap.add_argument("--m", type=int, default=0,
                     help="query count (default: --n; smaller sizes only for profiling runs)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f64x"],
@@ -851,9 +944,17 @@ def main():
                          "profiling)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the FP64, end-to-end and CPU-baseline measurements")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="with N > 1 ranks: weak = every rank its own full query set; strong = "
+                         "the workload's queries split over the ranks")
+    ap.add_argument("--leg", default="all", choices=["all", "batched"],
+                    help="batched: the 256-dataset batched workload alone, for profiling the "
+                         "batch kernel (with --no-extras: built-in shape, no autotuning)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg == "batched":
+        return run_batched_leg(args)
     return run_gpu(args)
 
 

@@ -237,15 +237,16 @@ typedef struct aidw_tune_config {
     int32_t knn_queries_per_thread; /* pruned phase 1: 2 or 4 queries per thread (query block
                                  * 128x), 0 = 4 for lists of up to 16, else 2; lists of 32
                                  * always take 2 */
-    int32_t unit_order;         /* batches: 0 = all phase-1 units, then all phase-2 units;
-                                 * 1 = phase-2 units of each item interleaved with phase-1
-                                 * units of items further down the list (both phases run on
-                                 * the SMs at once) */
+    int32_t unit_order;         /* batches: which units a persistent CTA takes first.
+                                 * 0 = every CTA takes the next phase-2 unit as soon as its
+                                 * inputs are complete, phase-1 units while they are not;
+                                 * 1 = the same, except that one CTA in four takes phase-1
+                                 * units first (phase 1 runs ahead on part of the SMs) */
     int32_t reserved;           /* zero */
 } aidw_tune_config;
 
 /* Fills the built-in shape: 2 queries per thread in both phases, 512-point tiles, the smallest
- * list, 65,536 points per batch work unit, full occupancy, phase-by-phase unit order. */
+ * list, 65,536 points per batch work unit, full occupancy, unit order 0. */
 int aidw_tune_config_default(aidw_tune_config *out);
 /* AIDW_OK if every field is one of the values above, else AIDW_ERR_INVALID_ARG. */
 int aidw_tune_config_check(const aidw_tune_config *cfg);
@@ -311,8 +312,9 @@ int aidw_tune_cache_load(const char *path);
  * device footprint fits the serving budget and packs them into persistent batch launches
  * (continuous batching: a new launch starts on another stream while earlier ones still run).
  * An FP32 request's result does not depend on what it was batched with. FP64 requests and
- * requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests)
- * is full; a request larger than the whole budget finishes with AIDW_ERR_OOM. */
+ * requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests
+ * unless configured otherwise) is full: the request was not accepted, and the caller resubmits
+ * later or sheds it; a request larger than the whole budget finishes with AIDW_ERR_OOM. */
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
                 const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
                 aidw_request *out_id);
@@ -333,9 +335,16 @@ int aidw_release_request(aidw_ctx *ctx, aidw_request id);
 /* Shapes the serving runtime; call before the first aidw_submit (INVALID_ARG afterwards).
  * inflight_bytes: device memory that admitted requests may hold at once (0: half of the
  * context's budget, or 8 GiB without one); max_batch_requests: requests per launch (0: 256);
- * streams: launches that may run at once (0: 2, at most 8). */
+ * streams: launches that may run at once (0: 2, at most 8); max_queued: requests that may wait
+ * for admission at once (0: the context's current limit, 4,096 unless changed by
+ * aidw_serving_set_queue_limit), beyond which aidw_submit returns AIDW_ERR_AGAIN. */
 int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_batch_requests,
-                           int32_t streams);
+                           int32_t streams, int64_t max_queued);
+
+/* Changes the serving queue's length (requests waiting for admission; >= 1) at any time,
+ * before or after the first aidw_submit: later submits see the new limit, requests already
+ * queued stay queued (a shorter limit only refuses new ones). INVALID_ARG for max_queued < 1. */
+int aidw_serving_set_queue_limit(aidw_ctx *ctx, int64_t max_queued);
 
 typedef struct aidw_serving_stats {
     int64_t submitted;       /* requests accepted by aidw_submit */

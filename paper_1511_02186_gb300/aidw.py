@@ -132,7 +132,8 @@ SIGNATURES = {
     "aidw_wait": (ctypes.c_int, [_P, _I64, _I64]),
     "aidw_request_latency_us": (ctypes.c_int, [_P, _I64, _P]),
     "aidw_release_request": (ctypes.c_int, [_P, _I64]),
-    "aidw_serving_configure": (ctypes.c_int, [_P, ctypes.c_size_t, _I32, _I32]),
+    "aidw_serving_configure": (ctypes.c_int, [_P, ctypes.c_size_t, _I32, _I32, _I64]),
+    "aidw_serving_set_queue_limit": (ctypes.c_int, [_P, _I64]),
     "aidw_serving_get_stats": (ctypes.c_int, [_P, _P]),
     "aidw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "aidw_check_device_errors": (ctypes.c_int, [_P]),
@@ -552,10 +553,15 @@ class Context:
         return rc
 
     def serving_configure(self, inflight_bytes: int = 0, max_batch_requests: int = 0,
-                          streams: int = 0):
+                          streams: int = 0, max_queued: int = 0):
         _check(self.lib.aidw_serving_configure(self.ptr, int(inflight_bytes),
-                                               int(max_batch_requests), int(streams)),
+                                               int(max_batch_requests), int(streams),
+                                               int(max_queued)),
                "serving_configure")
+
+    def serving_set_queue_limit(self, max_queued: int):
+        _check(self.lib.aidw_serving_set_queue_limit(self.ptr, int(max_queued)),
+               "serving_set_queue_limit")
 
     def serving_stats(self) -> ServingStats:
         s = ServingStats()

@@ -116,6 +116,7 @@ struct aidw_ctx {
     int wslots_cache[3][3][2] = {};  // [precision][queries per thread 2/4/8][tile 256/512]
     aidw_tune_config tune = aidw::tune_default();
     ServingRuntime *serving = nullptr;
+    int64_t serving_queue_limit = 4096;  // requests waiting for admission at most
 };
 
 namespace aidw {
@@ -1135,5 +1136,9 @@ ServingRuntime *&ctx_serving(aidw_ctx *ctx)
 std::mutex &ctx_mutex(aidw_ctx *ctx)
 {
     return ctx->mu;
+}
+int64_t &ctx_serving_queue_limit(aidw_ctx *ctx)
+{
+    return ctx->serving_queue_limit;
 }
 }  // namespace aidw

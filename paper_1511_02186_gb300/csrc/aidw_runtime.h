@@ -41,6 +41,8 @@ int ctx_device(aidw_ctx *ctx);
 int ctx_sm_count(aidw_ctx *ctx);
 ServingRuntime *&ctx_serving(aidw_ctx *ctx);
 std::mutex &ctx_mutex(aidw_ctx *ctx);
+// Serving queue length (read and written under ctx_mutex).
+int64_t &ctx_serving_queue_limit(aidw_ctx *ctx);
 
 bool dataset_lookup(aidw_ctx *ctx, int64_t id, DatasetDev *dev, double *r_exp);
 int pointer_kind(const void *p, int device);
@@ -86,7 +88,10 @@ struct BatchState {
     void *d_units = nullptr;  // work list
     uint32_t *d_counters = nullptr;  // [0] work counter, then per-item counters
     size_t counter_bytes = 0;
-    int n_units = 0;
+    int n_units = 0;   // phase-1 and phase-2 units
+    int n_units1 = 0;  // phase-1 units (the first n_units1 of the work list)
+    bool lean = false;  // the 64-register kernel variant serves this batch
+    bool order_in_tz = false;  // pruned units keep their tile order in the phase-2 z buffers
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
     // Batch-wide query ordering (Z-order within each item).

@@ -290,6 +290,62 @@ __device__ __forceinline__ bool knn_unit(const DatasetDev &ds, int64_t m, int64_
 // k-th distance.
 // ---------------------------------------------------------------------------------------------
 
+// Eq. 3-6 and the phase-2 parameters of one query from its k nearest squared distances d[0..k)
+// (ascending, each offset by kEpsF32): r_obs as an FP32 pairwise sum of the distances, R, mu and
+// alpha in FP64. Writes alpha to *alpha.
+__device__ __forceinline__ QParamF32 select_params(const float *d, int k, double r_exp,
+                                                   const AlphaMap &am, double *alpha_out)
+{
+    const float d1 = d[0];
+    // Eq. 3: mean of the k distances; sqrt of (d2 - eps) undoes the coincidence offset.
+    float v[AIDW_MAX_K];
+    for (int r = 0; r < k; ++r)
+        v[r] = __fsqrt_rn(__fsub_rn(d[r], kEpsF32));
+    for (int stride = 1; stride < k; stride *= 2)
+        for (int i = 0; i + stride < k; i += 2 * stride)
+            v[i] = __fadd_rn(v[i], v[i + stride]);
+    const double r_obs = static_cast<double>(v[0]) / k;
+    const double R = r_obs / r_exp;           // Eq. 4
+    const double mu = membership_eq5(R, am);  // Eq. 5
+    const double alpha = alpha_eq6(mu, am);   // Eq. 6
+
+    const float L1 = lg2_approx(d1);
+    QParamF32 o;
+    if (d1 == kEpsF32) {
+        // Coincident query: weight 1 on every coincident point, 0 elsewhere.
+        o.neg_s = -kCoincScaleF32;
+        o.c = kCoincScaleF32 * L1;
+    } else {
+        const float sh = static_cast<float>(0.5 * alpha);
+        o.neg_s = -sh;
+        o.c = sh * L1;
+    }
+    *alpha_out = alpha;
+    return o;
+}
+
+// Selection fused into a pruned phase-1 unit (one unit holds every list of its queries, so
+// no merge is needed): Eq. 3-6 straight from the register lists, the phase-2 parameters to
+// qparam[q] and alpha to out_alpha[perm[q]] (nullable); the lists themselves are not stored.
+struct FusedSelect {
+    double r_exp;
+    AlphaMap am;
+    QParamF32 *qparam;
+    float *out_alpha;
+    const uint32_t *perm;  // Z-order position -> caller's query index
+};
+
+// One query of a fused selection (kept out of line: it runs once per query, and inlined into
+// the scan it would lengthen the scan's register life ranges).
+static __device__ __noinline__ void fused_select_query(const float *d, int k,
+                                                       const FusedSelect *fs, int64_t q)
+{
+    double alpha;
+    fs->qparam[q] = select_params(d, k, fs->r_exp, fs->am, &alpha);
+    if (fs->out_alpha)
+        fs->out_alpha[fs->perm[q]] = static_cast<float>(alpha);
+}
+
 // Shared-memory scratch of a pruned phase-1 unit.
 struct CullShared {
     float red[4][kThreads / 32];
@@ -311,7 +367,8 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
                                               int *__restrict__ err,
                                               float4 (*tile)[kTileF32Knn], TileSeq &ts,
                                               unsigned long long *order, int32_t *idx_smem,
-                                              CullShared &cs)
+                                              CullShared &cs,
+                                              const FusedSelect *fsel = nullptr)
 {
     constexpr int H = Q / 2;
     constexpr int W = kThreads / 32;
@@ -494,6 +551,27 @@ __device__ __forceinline__ bool knn_cull_unit(const DatasetDev &ds, int64_t m, i
     __syncthreads();
     if (!ok)
         return false;
+    if (!IDX && fsel) {
+        // The same k values, in the same order, as a one-split merge would read back.
+        float d[Q][AIDW_MAX_K];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+#pragma unroll
+            for (int r0 = 0; r0 < KP; ++r0) {
+                const int r = r0 - (KP - k);
+                if (r >= 0)
+                    d[j][r] = L[j][r0];
+            }
+        }
+#pragma unroll 1
+        for (int j = 0; j < Q; ++j) {
+            const int64_t q = wbase + j * 32;
+            if (q >= m)
+                continue;
+            fused_select_query(d[j], k, fsel, q);
+        }
+        return true;
+    }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int64_t q = wbase + j * 32;
@@ -555,31 +633,8 @@ __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k,
             hi[bs] = INT32_MAX;
         }
     }
-    const float d1 = d[0];
-    // Eq. 3: mean of the k distances; sqrt of (d2 - eps) undoes the coincidence offset.
-    float v[AIDW_MAX_K];
-    for (int r = 0; r < k; ++r)
-        v[r] = __fsqrt_rn(__fsub_rn(d[r], kEpsF32));
-    for (int stride = 1; stride < k; stride *= 2)
-        for (int i = 0; i + stride < k; i += 2 * stride)
-            v[i] = __fadd_rn(v[i], v[i + stride]);
-    const double r_obs = static_cast<double>(v[0]) / k;
-    const double R = r_obs / r_exp;           // Eq. 4
-    const double mu = membership_eq5(R, am);  // Eq. 5
-    const double alpha = alpha_eq6(mu, am);   // Eq. 6
-
-    const float L1 = lg2_approx(d1);
-    QParamF32 o;
-    if (d1 == kEpsF32) {
-        // Coincident query: weight 1 on every coincident point, 0 elsewhere.
-        o.neg_s = -kCoincScaleF32;
-        o.c = kCoincScaleF32 * L1;
-    } else {
-        const float sh = static_cast<float>(0.5 * alpha);
-        o.neg_s = -sh;
-        o.c = sh * L1;
-    }
-    qp[q] = o;
+    double alpha;
+    qp[q] = select_params(d, k, r_exp, am, &alpha);
     if (out_alpha)
         out_alpha[qo] = static_cast<float>(alpha);
 }

@@ -368,6 +368,7 @@ ServingRuntime *ensure_serving(aidw_ctx *ctx)
         rt = new ServingRuntime();
         rt->ctx = ctx;
         rt->cfg = cfg;
+        rt->max_queue = static_cast<size_t>(ctx_serving_queue_limit(ctx));
         if (left != SIZE_MAX)
             rt->budget = left / 2;
         cudaSetDevice(ctx_device(ctx));
@@ -452,9 +453,9 @@ int aidw_debug_admission(int64_t count, const int32_t *solo, const uint64_t *foo
 }
 
 int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_batch_requests,
-                           int32_t streams)
+                           int32_t streams, int64_t max_queued)
 {
-    if (!ctx || max_batch_requests < 0 || streams < 0 || streams > 8)
+    if (!ctx || max_batch_requests < 0 || streams < 0 || streams > 8 || max_queued < 0)
         return AIDW_ERR_INVALID_ARG;
     {
         std::lock_guard<std::mutex> g(ctx_mutex(ctx));
@@ -469,6 +470,9 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
         rt = new ServingRuntime();
         rt->ctx = ctx;
         rt->cfg = cfg;
+        if (max_queued)
+            ctx_serving_queue_limit(ctx) = max_queued;
+        rt->max_queue = static_cast<size_t>(ctx_serving_queue_limit(ctx));
         if (inflight_bytes)
             rt->budget = inflight_bytes;
         if (max_batch_requests)
@@ -484,6 +488,23 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
         ctx_serving(ctx) = rt;
     }
     rt->worker = std::thread(worker_main, rt);
+    return AIDW_OK;
+}
+
+int aidw_serving_set_queue_limit(aidw_ctx *ctx, int64_t max_queued)
+{
+    if (!ctx || max_queued < 1)
+        return AIDW_ERR_INVALID_ARG;
+    ServingRuntime *rt;
+    {
+        std::lock_guard<std::mutex> g(ctx_mutex(ctx));
+        ctx_serving_queue_limit(ctx) = max_queued;
+        rt = ctx_serving(ctx);
+    }
+    if (rt) {
+        std::lock_guard<std::mutex> g(rt->mu);
+        rt->max_queue = static_cast<size_t>(max_queued);
+    }
     return AIDW_OK;
 }
 
@@ -522,6 +543,16 @@ int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, 
     r.host_out = ko == 0;
     r.host_alpha = out_alpha && ka == 0;
     r.solo = p->precision != AIDW_F32C || out_knn != nullptr;
+    ServingRuntime *rt = ensure_serving(ctx);
+    {
+        // Refuse early when the queue is full, before the O(m) scan of host inputs below (the
+        // decisive check is repeated under the same lock when the request is queued).
+        std::lock_guard<std::mutex> g(rt->mu);
+        if (rt->queue.size() >= rt->max_queue) {
+            ++rt->stats.rejected_again;
+            return AIDW_ERR_AGAIN;
+        }
+    }
     if (r.host_qx || r.host_qy) {
         for (int64_t i = 0; i < m; ++i) {
             const float a = static_cast<const float *>(qx)[i];
@@ -530,7 +561,6 @@ int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, 
                 return AIDW_ERR_INVALID_ARG;
         }
     }
-    ServingRuntime *rt = ensure_serving(ctx);
     r.footprint = request_footprint(r, dev.n_pad, rt->cfg);
     {
         std::lock_guard<std::mutex> g(rt->mu);

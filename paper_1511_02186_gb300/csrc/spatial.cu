@@ -101,29 +101,83 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift, uint3
     counts[static_cast<int64_t>(tid) * nblocks + blockIdx.x] = h[tid];
 }
 
-// Exclusive scan of counts[0..total) in place, by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *counts, int64_t total)
+// Exclusive scan of the digit counts in two levels: segments of kScanSeg counts are scanned in
+// place by one block each (segment-local prefixes), the segment totals by one block; the
+// scatter adds the two. (One block scanning all counts sequentially took 0.4 ms per pass at
+// 3.8M keys; most of a batch's query ordering.)
+constexpr int kScanThreads = 1024;
+constexpr int kScanSeg = 4 * kScanThreads;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot,
+                                                         uint32_t *total)
 {
-    __shared__ uint32_t part[1024];
-    const int tid = threadIdx.x;
-    const int64_t per = (total + 1023) / 1024;
-    const int64_t b = tid * per, e = min(b + per, total);
-    uint32_t s = 0;
-    for (int64_t i = b; i < e; ++i)
-        s += counts[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = tid >= off ? part[tid - off] : 0u;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += t;
     }
-    uint32_t run = part[tid] - s;
-    for (int64_t i = b; i < e; ++i) {
-        const uint32_t c = counts[i];
-        counts[i] = run;
-        run += c;
+    if (lane == 31)
+        warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += t;
+        }
+        if (lane < kScanThreads / 32)
+            warp_tot[lane] = wi - w;
+        if (lane == 31)
+            *total = wi;
+    }
+    __syncthreads();
+    return warp_tot[warp] + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+radix_scan_local_kernel(uint32_t *counts, int64_t total, uint32_t *seg_sums)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t seg_total;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kScanSeg + 4 * threadIdx.x;
+    uint32_t c[4];
+    uint32_t t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = i0 + j < total ? counts[i0 + j] : 0u;
+        t += c[j];
+    }
+    uint32_t run = block_exclusive_scan(t, warp_tot, &seg_total);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (i0 + j < total)
+            counts[i0 + j] = run;
+        run += c[j];
+    }
+    if (threadIdx.x == 0)
+        seg_sums[blockIdx.x] = seg_total;
+}
+
+// Exclusive scan of the segment totals in place, by one block.
+__global__ void __launch_bounds__(kScanThreads) radix_scan_top_kernel(uint32_t *seg, int64_t n)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t chunk_total;
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < n; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t v = i < n ? seg[i] : 0u;
+        const uint32_t ex = block_exclusive_scan(v, warp_tot, &chunk_total);
+        if (i < n)
+            seg[i] = carry + ex;
+        carry += chunk_total;
+        __syncthreads();
     }
 }
 
@@ -131,14 +185,16 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *counts, int6
 __global__ void __launch_bounds__(kSortThreads)
 radix_scatter_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                      uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
-                     int shift, const uint32_t *__restrict__ offsets, int nblocks)
+                     int shift, const uint32_t *__restrict__ offsets,
+                     const uint32_t *__restrict__ seg_offsets, int nblocks)
 {
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t base_off[256];
     __shared__ uint32_t running[256];
     __shared__ uint32_t wcount[W][256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    base_off[tid] = offsets[static_cast<int64_t>(tid) * nblocks + blockIdx.x];
+    const int64_t oi = static_cast<int64_t>(tid) * nblocks + blockIdx.x;
+    base_off[tid] = offsets[oi] + seg_offsets[oi / kScanSeg];
     running[tid] = 0;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
@@ -243,7 +299,10 @@ inline unsigned grid_for(int64_t n, int threads, int cap)
 size_t radix_scratch_bytes(int64_t n)
 {
     const int64_t nblocks = (n + kSortTile - 1) / kSortTile;
-    return sizeof(uint32_t) * (2 * static_cast<size_t>(n) + 256 * static_cast<size_t>(nblocks));
+    const int64_t nseg = (256 * nblocks + kScanSeg - 1) / kScanSeg;
+    return sizeof(uint32_t) *
+           (2 * static_cast<size_t>(n) + 256 * static_cast<size_t>(nblocks) +
+            static_cast<size_t>(nseg));
 }
 
 // Sorts (keys, vals)[0..n) stably by the low `bits` bits of the key (rounded up to a multiple
@@ -258,13 +317,18 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, void *tm
     uint32_t *k2 = static_cast<uint32_t *>(tmp);
     uint32_t *v2 = k2 + n;
     uint32_t *counts = v2 + n;
+    const int64_t ncounts = static_cast<int64_t>(nblocks) * 256;
+    const int64_t nseg = (ncounts + kScanSeg - 1) / kScanSeg;
+    uint32_t *seg = counts + ncounts;
     uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     const int top = bits <= 16 ? 16 : 32;
     for (int shift = 0; shift < top; shift += 8) {
         radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, n, shift, counts, nblocks);
-        radix_scan_kernel<<<1, 1024, 0, st>>>(counts, static_cast<int64_t>(nblocks) * 256);
+        radix_scan_local_kernel<<<static_cast<unsigned>(nseg), kScanThreads, 0, st>>>(
+            counts, ncounts, seg);
+        radix_scan_top_kernel<<<1, kScanThreads, 0, st>>>(seg, nseg);
         radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts,
-                                                               nblocks);
+                                                               seg, nblocks);
         uint32_t *t = ka;
         ka = kb;
         kb = t;

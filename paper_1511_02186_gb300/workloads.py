@@ -203,3 +203,33 @@ def served_requests(datasets: list[Workload], seed: int = 1, rate: float = 2000.
         qy = rng.uniform(0.0, side, m)
         out.append((t, d, qx, qy))
     return out
+
+
+def served_arrivals(datasets: list[Workload], seed: int = 1, rate: float = 2000.0,
+                    duration_s: float = 10.0, m_lo: int = 256, m_hi: int = 262144):
+    """Poisson arrivals without their query arrays: list of (arrival_time_s, dataset_index,
+    query_count), query counts log-uniform in [m_lo, m_hi]. The queries come from
+    ``served_query_pool`` (long runs would not fit in host memory with one array per
+    request)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration_s:
+            break
+        d = int(rng.integers(0, len(datasets)))
+        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        out.append((t, d, m))
+    return out
+
+
+def served_query_pool(datasets: list[Workload], seed: int = 2, size: int = 262144):
+    """Per dataset, `size` float32 query points uniform in its square; a request of m queries
+    takes a contiguous slice of its dataset's pool."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for w in datasets:
+        side = math.sqrt(w.area)
+        out.append((rng.uniform(0.0, side, size).astype(np.float32),
+                    rng.uniform(0.0, side, size).astype(np.float32)))
+    return out

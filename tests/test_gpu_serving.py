@@ -209,3 +209,48 @@ def test_full_size_served_workload_sampled():
         assert worst <= TOL_F32, worst
         st = ctx.serving_stats()
         assert st.completed == len(subs) and st.failed == 0
+
+
+def test_backpressure_queue_full_then_resubmit():
+    """A queue of 3 requests served one request per launch on one stream: a burst of submits
+    overfills it, aidw_submit refuses with AIDW_ERR_AGAIN (nothing accepted, counted in the
+    stats) and the client resubmits after a pause; every request then completes and matches the
+    oracle. A longer limit set while the runtime is running takes the next burst whole."""
+    with aidw.Context(0) as ctx:
+        ctx.serving_configure(max_batch_requests=1, streams=1, max_queued=3)
+        dss = datasets(ctx, 6, 2, n_max=20000)
+        p = aidw.default_params(k=10)
+        reqs = [request(dss[i % 2][0], 1200 + i, 3000, device=False) + (dss[i % 2][1],)
+                for i in range(24)]
+        accepted, again = [], 0
+        for w, (qx, qy), out, ds in reqs:
+            while True:
+                rc, rid = ctx.submit(ds, qx, qy, p, out)
+                if rc != aidw.ERR_AGAIN:
+                    break
+                assert rid == 0
+                again += 1
+                time.sleep(0.0005)
+            assert rc == aidw.OK
+            accepted.append((w, rid, out))
+        assert again >= 1, "a burst of 24 should overfill a queue of 3"
+        for w, rid, out in accepted:
+            assert ctx.wait(rid, 60_000_000) == aidw.OK
+            ref, _ = oracle_for(w, aidw.F32C)
+            assert rel_err(out, ref).max() <= TOL_F32
+            assert ctx.release(rid) == aidw.OK
+        st = ctx.serving_stats()
+        assert st.rejected_again == again
+        assert st.completed == 24 and st.failed == 0 and st.queued == 0
+        # A longer queue, set while the runtime runs: the same burst is taken without refusal.
+        ctx.serving_set_queue_limit(64)
+        ids = []
+        for w, (qx, qy), out, ds in reqs:
+            rc, rid = ctx.submit(ds, qx, qy, p, out)
+            assert rc == aidw.OK
+            ids.append(rid)
+        for rid in ids:
+            assert ctx.wait(rid, 60_000_000) == aidw.OK
+        assert ctx.serving_stats().rejected_again == again
+        with pytest.raises(aidw.AidwError):
+            ctx.serving_set_queue_limit(0)

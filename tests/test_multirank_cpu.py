@@ -75,3 +75,68 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert obj["impl"] == "reference" and obj["n_gpus"] == 2
     assert obj["value"] > 0 and obj["cpu_baseline"]["kind"] == "oracle"
     assert obj["e2e"]["h2d_bytes_per_step"] == 0
+
+
+# ---- query sharding (paper_1511_02186_gb300.sharding) ----------------------------------------
+
+def test_query_ranges_cover_every_query_once():
+    from paper_1511_02186_gb300.sharding import query_ranges
+    for m in (0, 1, 2, 7, 1000, 1 << 20, 1048577):
+        for world in (1, 2, 3, 4, 7, 8):
+            rs = query_ranges(m, world)
+            assert len(rs) == world and rs[0][0] == 0 and rs[-1][1] == m
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            sizes = [e - b for b, e in rs]
+            assert min(sizes) >= 0 and max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        query_ranges(5, 0)
+
+
+def _shard_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    import oracle
+    from paper_1511_02186_gb300 import sharding, workloads
+    bench.dist_setup(world)
+    wl = workloads.small_case(41, 3000, 1001, k=7, pattern="clustered")
+
+    def compute(a, b):  # the per-rank compute of this test: the oracle on the rank's slice
+        r = oracle.interpolate(wl.x, wl.y, wl.z, wl.area, a, b, wl.k, threads=1)
+        return {"z": r["z"], "alpha": r["alpha"], "knn": r["knn"]}
+
+    b, e, own = sharding.shard_interpolate(compute, wl.qx, wl.qy, rank, world, gather=False)
+    b0, e0, full = sharding.shard_interpolate(compute, wl.qx, wl.qy, rank, world, gather=True)
+    q.put((rank, b, e, b0, e0, {k: v.tolist() for k, v in full.items()}))
+    dist.destroy_process_group()
+
+
+def test_sharded_results_equal_the_single_rank_result():
+    """Two gloo ranks each interpolate their contiguous range of 1,001 queries (the oracle as
+    the per-rank compute); the gathered arrays equal the one-rank result element for element,
+    in the caller's order."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_1511_02186_gb300 import workloads
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_shard_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    wl = workloads.small_case(41, 3000, 1001, k=7, pattern="clustered")
+    ref = oracle.interpolate(wl.x, wl.y, wl.z, wl.area, wl.qx, wl.qy, wl.k, threads=1)
+    assert [(g[1], g[2]) for g in got] == [(0, 501), (501, 1001)]
+    for rank, b, e, b0, e0, full in got:
+        assert (b0, e0) == (0, wl.m)
+        assert np.array_equal(np.asarray(full["z"]), ref["z"])
+        assert np.array_equal(np.asarray(full["alpha"]), ref["alpha"])
+        assert np.array_equal(np.asarray(full["knn"]), ref["knn"])
