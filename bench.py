@@ -256,7 +256,7 @@ def oracle_rate_small(wl, threads):
 
 # ---- batched and served configurations -------------------------------------------------------
 
-def bench_batched(ctx, steps: int, warmup: int, dev, stream, tune: bool = True):
+def bench_batched(ctx, steps: int, warmup: int, dev, stream, tune: bool = True, peak=None):
     """256 independent datasets (n log-uniform in [1,024, 262,144], m log-uniform in
     [1,024, 65,536], side log-uniform in [10, 1000], uniform or clustered, k in {6, 10, 15}) in
     one persistent launch replayed from a CUDA graph: timed with the built-in kernel shape,
@@ -306,6 +306,8 @@ def bench_batched(ctx, steps: int, warmup: int, dev, stream, tune: bool = True):
             "tuned_config": cfg.as_dict(), "autotune_s": tune_s,
             "default_config_ms_per_launch": ms_default,
             "default_config_value": pairs / (ms_default / 1e3),
+            "frac_of_phase2_bound": None if peak is None else pairs / (ms / 1e3) / peak,
+            "phase2_bound": peak,
             "launch": "one persistent work-queue kernel per batch, replayed from a CUDA graph; "
                       "kernel shape chosen by the autotuner on this batch"}
 
@@ -783,7 +785,7 @@ def run_gpu(args):
     h2d = 3 * 8 * wl.n + 2 * 4 * wl.m
     d2h = 4 * wl.m
 
-    batched = bench_batched(ctx, max(2, args.steps), args.warmup, dev, stream)
+    batched = bench_batched(ctx, max(2, args.steps), args.warmup, dev, stream, peak=peak)
     stress = bench_precision_stress(ctx, dev, stream)
     designs = bench_paper_designs(ctx, dev, stream)
     idw = bench_standard_idw(ctx, ds, wl, dev, stream, peak)
@@ -862,7 +864,15 @@ def run_gpu(args):
                                                       "instructions per clk per SM (nominal "
                                                       "1.25 TFLOP/s; ncu's FP64 pipe peak) / "
                                                       f"{FP64_OPS_P2} FP64 instructions per "
-                                                      "pair")}},
+                                                      "pair"),
+                                       "floor_peak": fp64x_w_peak,
+                                       "frac_of_floor": fp64_w_achieved / fp64x_w_peak,
+                                       "floor_basis": (f"the same FP64 pipe at {FP64X_OPS_P2} "
+                                                       "FP64 instructions per pair, the fewest "
+                                                       "a pair needs at the FP64 bar as the "
+                                                       "FP64X design shows (the squared "
+                                                       "distance in FP64, the rest in "
+                                                       "double-float on the FP32 pipes)")}},
             "fp64x_path": {"value": fp64x_rate, "unit": UNIT,
                            "sample": f"{q64x} seeded queries x all {wl.n} data points",
                            "kernel_ms": {"knn_incl_query_ordering": kt64x.knn_ms,

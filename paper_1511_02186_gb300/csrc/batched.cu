@@ -71,6 +71,10 @@ struct BatchItemDev {
 
 struct WorkUnit {
     int32_t item, qblock, split, type;
+    // Phase-2 units: the counter that completes their inputs and its target value (read by the
+    // scheduler without touching the item table).
+    uint32_t target, reserved;
+    const uint32_t *counter;
 };
 
 // Every thread's results are made visible at GPU scope before thread 0 counts the unit done.
@@ -110,14 +114,12 @@ __device__ __noinline__ bool batch_weights_unit(const BatchItemDev *itp, int qbl
 // Largest tile count whose pruned-scan tile order (8 bytes a tile) fits in g_tz.
 constexpr int kOrderInTz = static_cast<int>(sizeof(g_tz) / sizeof(unsigned long long));
 
-// Whether a phase-2 unit's inputs are complete (thread 0; acquire loads, so that the CTA reads
+// Whether a phase-2 unit's inputs are complete (thread 0; an acquire load, so that the CTA reads
 // the producers' results after the following barrier): a WEIGHTS unit needs its item's phase 1
 // (every query block selected), a FINAL unit the WEIGHTS units of its query block.
-__device__ __forceinline__ bool p2_ready(const BatchItemDev &it, const WorkUnit &wu)
+__device__ __forceinline__ bool p2_ready(const WorkUnit &wu)
 {
-    if (wu.type == kUnitWeights)
-        return ld_acquire(it.cnt_ready) >= static_cast<uint32_t>(it.knn.qblocks);
-    return ld_acquire(&it.cnt_w[wu.qblock]) >= static_cast<uint32_t>(it.w.splits);
+    return ld_acquire(wu.counter) >= wu.target;
 }
 
 // What a CTA does next (decided by thread 0, shared through shared memory).
@@ -185,7 +187,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 if (p2) {
                     // Peek at the next phase-2 unit; phase 1 while it cannot run yet.
                     const int h = static_cast<int>(*reinterpret_cast<volatile uint32_t *>(next2));
-                    p2 = h >= n2 || p2_ready(items[units2[h].item], units2[h]);
+                    p2 = h >= n2 || p2_ready(units2[h]);
                 }
                 if (!p2 && !take_p1())
                     p2 = true;
@@ -196,7 +198,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
                 }
             }
             if (pending >= 0) {
-                if (p2_ready(items[units2[pending].item], units2[pending])) {
+                if (p2_ready(units2[pending])) {
                     kind = kRunP2;
                     unit = pending;
                     pending = -1;
@@ -226,7 +228,7 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
             if (tid == 0) {
                 bool got = false;
                 for (uint32_t i = 0; i < kMaxWaitPolls; ++i) {
-                    if (p2_ready(items[w2.item], w2)) {
+                    if (p2_ready(w2)) {
                         got = true;
                         break;
                     }
@@ -320,10 +322,10 @@ f32_batch_kernel(const BatchItemDev *__restrict__ items, const WorkUnit *__restr
             const int64_t p1 = min(p0 + it.w.split_len, it.ds.n_pad);
             if (tw == 256) {
                 ok = batch_weights_unit<QW, 256>(&it, wu.qblock, wu.split, err, ts.seq);
-                ts.seq += static_cast<uint32_t>((p1 - p0) / 256);
+                ts.seq += static_cast<uint32_t>(weights_tiles<256>(it.ds, p0, p1));
             } else {
                 ok = batch_weights_unit<QW, kTileF32W>(&it, wu.qblock, wu.split, err, ts.seq);
-                ts.seq += static_cast<uint32_t>((p1 - p0) / kTileF32W);
+                ts.seq += static_cast<uint32_t>(weights_tiles<kTileF32W>(it.ds, p0, p1));
             }
             if (ok)
                 cta_publish(&it.cnt_w[wu.qblock]);
@@ -629,6 +631,17 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
         d.cnt_knn = c;
         d.cnt_ready = c + d.knn.qblocks;
         d.cnt_w = c + d.knn.qblocks + 1;
+    }
+    for (size_t j = n1; j < u.size(); ++j) {
+        WorkUnit &w = u[j];
+        const BatchItemDev &d = h[w.item];
+        if (w.type == kUnitWeights) {
+            w.counter = d.cnt_ready;
+            w.target = static_cast<uint32_t>(d.knn.qblocks);
+        } else {
+            w.counter = d.cnt_w + w.qblock;
+            w.target = static_cast<uint32_t>(d.w.splits);
+        }
     }
     bs->count = count;
     bs->total_q = total_q;

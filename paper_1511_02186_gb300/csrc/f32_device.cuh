@@ -646,8 +646,27 @@ __device__ __forceinline__ void select_query(int64_t q, int64_t m, int S, int k,
 // squared distance, i.e. (d1/d)^alpha <= 1: the ratio of Eq. 1 is unchanged and nothing
 // overflows. Each thread sums kChunkW points per query in plain FP32 and merges the chunk sums
 // by Kahan steps; the partial sums of the split go to part_sum[s][0..3][q]. Tiles of TW points
-// hold whole chunks, so neither Q nor TW changes any query's sequence of operations.
+// hold whole chunks, so neither Q nor TW changes any query's sequence of operations. Chunks
+// that hold only padding (from the first multiple of kChunkW at or above n) are not summed:
+// they would add weights of exactly 0; tiles made of them are not loaded.
 // ---------------------------------------------------------------------------------------------
+
+// End of the summed chunks of a split [p_begin, p_end): the dataset's last real point rounded
+// up to a whole chunk.
+__device__ __forceinline__ int64_t weights_end(const DatasetDev &ds, int64_t p_end)
+{
+    return min(p_end, (ds.n + kChunkW - 1) / kChunkW * kChunkW);
+}
+
+// Tiles of TW points a phase-2 unit over [p_begin, p_end) loads.
+template <int TW>
+__device__ __forceinline__ int weights_tiles(const DatasetDev &ds, int64_t p_begin,
+                                             int64_t p_end)
+{
+    const int64_t e = weights_end(ds, p_end);
+    return e > p_begin ? static_cast<int>((e - p_begin + TW - 1) / TW) : 0;
+}
+
 template <int Q, int TW>
 __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, int64_t qbase,
                                              int64_t p_begin, int64_t p_end,
@@ -663,7 +682,8 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
     static_assert(TW % kChunkW == 0 && kPadPoints % TW == 0, "whole chunks, whole tiles");
     constexpr int H = Q / 2;
     const int tid = threadIdx.x;
-    const int ntiles = static_cast<int>((p_end - p_begin) / TW);
+    const int ntiles = weights_tiles<TW>(ds, p_begin, p_end);
+    const int64_t p_sum = weights_end(ds, p_end);
 
     float2 qxp[H], qyp[H], nsp[H], ccp[H];
     float hw[Q], cw[Q], hz[Q], cz[Q];
@@ -711,7 +731,9 @@ __device__ __forceinline__ bool weights_unit(const DatasetDev &ds, int64_t m, in
             ts.seq += ntiles;
             return false;
         }
-        for (int c = 0; c < TW; c += kChunkW) {
+        const int64_t t0 = p_begin + static_cast<int64_t>(t) * TW;
+        const int cend = static_cast<int>(min(static_cast<int64_t>(TW), p_sum - t0));
+        for (int c = 0; c < cend; c += kChunkW) {
             float2 sw[H], sz[H];
 #pragma unroll
             for (int h = 0; h < H; ++h)
