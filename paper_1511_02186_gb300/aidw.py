@@ -165,7 +165,7 @@ SIGNATURES = {
 # Test-only hooks exported by the library but not declared in the public header.
 DEBUG_SIGNATURES = {
     "aidw_debug_admission": (ctypes.c_int, [_I64, _P, _P, ctypes.c_uint64, ctypes.c_uint64, _I32,
-                                            _P]),
+                                            _P, _D, _P]),
     "aidw_debug_interpolate_splits": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P,
                                                      _I32, _I32]),
 }

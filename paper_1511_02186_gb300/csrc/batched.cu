@@ -443,11 +443,12 @@ constexpr int64_t kBatchKnnUnits = 128;
 // Phase-2 plan of a batch item: data splits of at most split_points points, and, for an item
 // with few queries, enough of them for about kBatchMinWeightUnits units of 256 queries, so
 // that an item alone (a lightly loaded server's flight) still spreads over every SM (a request
-// of 8,192 queries against 231,679 points with 65,536-point splits: 128 units for 608 resident
-// CTAs; served in 5.3 ms, with the extra splits in 2.7 ms, the one-shot call 2.5 ms). The split
-// length depends on the item's sizes and split_points only (not on the rest of the batch, nor
-// on the arithmetic-neutral shape fields).
-constexpr int64_t kBatchMinWeightUnits = 1024;
+// of 8,192 queries against 231,679 points with 65,536-point splits: 128 units; served in 5.3 ms,
+// with the extra splits in 2.7 ms, the one-shot call 2.5 ms). 512 units keep at least 3-4 CTAs
+// busy on every SM and make fewer, longer units than 1,024 (the 256-dataset batch: 70.7 against
+// 71.3 ms). The split length depends on the item's sizes and split_points only (not on the rest
+// of the batch, nor on the arithmetic-neutral shape fields).
+constexpr int64_t kBatchMinWeightUnits = 512;
 
 PassPlan batch_w_plan(int64_t m, int64_t n_pad, int qpb, int64_t split_points)
 {

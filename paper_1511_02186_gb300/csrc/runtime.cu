@@ -9,6 +9,15 @@
 // FP32 requests without a kNN output go through the batch kernel, whose per-item result does
 // not depend on the batch composition; FP64 requests and requests asking for neighbour indices
 // run alone through the one-shot path.
+//
+// A large FP32 request is cut into chunks of contiguous queries of about kChunkPairs
+// pair-evaluations each (the cut depends on the request's own sizes only, so its result is the
+// same alone and in any mix), and a flight takes at most one chunk of each queued request, in
+// arrival order, up to about kFlightPairs pair-evaluations in all. A launch then lasts tens of
+// milliseconds at most, and a small request arriving behind a large one waits for one flight
+// instead of the whole large request (a persistent batch kernel holds every SM until its work
+// runs out, so a launch on the other stream cannot start earlier).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -33,6 +42,15 @@ inline size_t align256(size_t b)
     return (b + 255) & ~static_cast<size_t>(255);
 }
 
+// Chunking of large requests and the work cap of one flight (pair-evaluations; about 14 ms and
+// 35 ms of the GPU at the batch kernel's rate). Measured on the served workload (64 datasets,
+// 256-262,144 queries a request) against no chunking: p99 80 against 99 ms at half the
+// capacity and 427 against 515 ms at 0.8 of it, throughput at 7x overload 2.63e12 against
+// 2.71e12 pair-evals/s; caps of 1.6e10 / 3.2e10 made flights so short (1.5 requests a launch)
+// that throughput at overload fell to 2.34e12 without a better p99.
+constexpr double kChunkPairs = 4e10;
+constexpr double kFlightPairs = 1e11;
+
 struct Request {
     int64_t ds = 0;
     const void *qx = nullptr, *qy = nullptr;
@@ -43,15 +61,25 @@ struct Request {
     int32_t *out_knn = nullptr;
     bool host_qx = false, host_qy = false, host_out = false, host_alpha = false;
     bool solo = false;  // FP64 or kNN output: runs through the one-shot path
-    size_t footprint = 0;
+    int64_t n_pad = 0;  // the dataset's padded size (chunk footprints)
+    int64_t n = 0;      // the dataset's size (chunk work)
+    int64_t chunk_m = 0;  // queries per chunk (the last one may hold fewer)
+    int32_t nchunks = 1, next_chunk = 0, chunks_done = 0;
+    size_t footprint = 0;  // of the largest chunk
     int status = AIDW_PENDING;
     bool done = false;
     Clock::time_point t_submit, t_done;
 };
 
+// One chunk of a request in a flight: queries [begin, end) of request id.
+struct Piece {
+    int64_t id;
+    int64_t begin, end;
+};
+
 struct Flight {
     bool busy = false;
-    std::vector<int64_t> ids;
+    std::vector<Piece> pieces;
     cudaEvent_t done_ev = nullptr;
     cudaStream_t stream = nullptr;
     void *pinned = nullptr;  // host staging (pinned), grown on demand
@@ -89,10 +117,12 @@ struct ServingRuntime {
 
 namespace {
 
-size_t request_footprint(const Request &r, int64_t n_pad, const aidw_tune_config &cfg)
+// Device bytes of `m` queries of request r in a flight: batch scratch plus host staging.
+size_t request_footprint(const Request &r, int64_t m_chunk, int64_t n_pad,
+                         const aidw_tune_config &cfg)
 {
-    size_t b = batch_item_bytes(n_pad, r.m, r.p.k, cfg) + 4096;
-    const size_t m = static_cast<size_t>(r.m);
+    size_t b = batch_item_bytes(n_pad, m_chunk, r.p.k, cfg) + 4096;
+    const size_t m = static_cast<size_t>(m_chunk);
     if (r.host_qx)
         b += align256(4 * m);
     if (r.host_qy)
@@ -104,30 +134,51 @@ size_t request_footprint(const Request &r, int64_t n_pad, const aidw_tune_config
     return b;
 }
 
+// Completes a whole request (status, time, statistics).
+void finish_request(ServingRuntime *rt, Request &r, int status, Clock::time_point now)
+{
+    if (r.status == AIDW_PENDING)
+        r.status = status;
+    r.done = true;
+    r.t_done = now;
+    if (r.status == AIDW_OK)
+        ++rt->stats.completed;
+    else
+        ++rt->stats.failed;
+}
+
 void finish(ServingRuntime *rt, const std::vector<int64_t> &ids, int status)
 {
     const auto now = Clock::now();
-    for (int64_t id : ids) {
-        Request &r = rt->reqs[id];
-        if (r.status == AIDW_PENDING)
+    for (int64_t id : ids)
+        finish_request(rt, rt->reqs[id], status, now);
+}
+
+// One launch's chunks have finished: a request is done once all its chunks are (its status is
+// its first error, if any).
+void finish_pieces(ServingRuntime *rt, const std::vector<Piece> &pieces, int status)
+{
+    const auto now = Clock::now();
+    for (const Piece &pc : pieces) {
+        Request &r = rt->reqs[pc.id];
+        if (status != AIDW_OK && r.status == AIDW_PENDING)
             r.status = status;
-        r.done = true;
-        r.t_done = now;
-        if (r.status == AIDW_OK)
-            ++rt->stats.completed;
-        else
-            ++rt->stats.failed;
+        if (++r.chunks_done == r.nchunks)
+            finish_request(rt, r, AIDW_OK, now);
     }
 }
 
-// Admission of the request at the head of the queue into the flight being assembled (pure host
-// logic; aidw_debug_admission runs it without a GPU). Requests are taken in arrival order: a
-// request that does not fit stops the flight (no overtaking), a request that could never fit
-// the budget fails with OOM, and FP64 / kNN-output requests run alone.
+// Admission of the next chunk of a queued request into the flight being assembled (pure host
+// logic; aidw_debug_admission runs it without a GPU). Queued requests are visited in arrival
+// order, one chunk each per flight: a chunk that does not fit stops the flight (no overtaking),
+// as does one that would take the flight's work above max_flight_pairs (unless the flight is
+// empty: a flight always takes its first chunk); a request that could never fit the budget
+// fails with OOM, and FP64 / kNN-output requests run alone.
 enum class Admit { kTake, kSolo, kRejectOom, kStop };
 
 Admit admission_step(bool solo, size_t footprint, size_t budget, size_t in_flight,
-                     size_t flight_bytes, size_t flight_count, int max_items)
+                     size_t flight_bytes, size_t flight_count, int max_items, double pairs,
+                     double flight_pairs, double max_flight_pairs)
 {
     if (static_cast<int64_t>(flight_count) >= max_items)
         return Admit::kStop;
@@ -136,6 +187,8 @@ Admit admission_step(bool solo, size_t footprint, size_t budget, size_t in_fligh
     if (footprint > budget)
         return Admit::kRejectOom;
     if (in_flight + flight_bytes + footprint > budget)
+        return Admit::kStop;
+    if (flight_count > 0 && max_flight_pairs > 0.0 && flight_pairs + pairs > max_flight_pairs)
         return Admit::kStop;
     return Admit::kTake;
 }
@@ -157,17 +210,19 @@ bool ensure_pinned(Flight &f, size_t bytes)
     return true;
 }
 
-// Launches the batch of requests `ids` on flight slot f. Called without the runtime lock; the
-// requests are owned by this launch until completion.
-int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &rq)
+// Launches the batch of request chunks `pc` (rq[i] owns pc[i]) on flight slot f. Called without
+// the runtime lock; the chunks are owned by this launch until completion.
+int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &rq,
+                  const std::vector<Piece> &pc)
 {
     NvtxScope range("aidw serving flight");
     aidw_ctx *ctx = rt->ctx;
     cudaStream_t st = f.stream;
     // Staging sizes.
     size_t host_bytes = 0, dev_bytes = 0;
-    for (const Request *r : rq) {
-        const size_t b = align256(4 * static_cast<size_t>(r->m));
+    for (size_t i = 0; i < rq.size(); ++i) {
+        const Request *r = rq[i];
+        const size_t b = align256(4 * static_cast<size_t>(pc[i].end - pc[i].begin));
         const size_t h = (r->host_qx ? b : 0) + (r->host_qy ? b : 0) + (r->host_out ? b : 0) +
                          (r->host_alpha ? b : 0);
         host_bytes += h;
@@ -186,36 +241,37 @@ int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &r
     bool ok = true;
     for (size_t i = 0; i < rq.size(); ++i) {
         const Request &r = *rq[i];
-        const size_t bytes = 4 * static_cast<size_t>(r.m), b = align256(bytes);
+        const int64_t b0 = pc[i].begin;
+        const size_t bytes = 4 * static_cast<size_t>(pc[i].end - b0), b = align256(bytes);
         aidw_batch_item &it = items[i];
         it.ds = r.ds;
-        it.m = r.m;
+        it.m = pc[i].end - b0;
         it.params = r.p;
-        it.qx = static_cast<const float *>(r.qx);
-        it.qy = static_cast<const float *>(r.qy);
-        it.out = static_cast<float *>(r.out);
-        it.out_alpha = r.out_alpha;
-        auto stage_in = [&](const void *src, const float **dst) {
+        it.qx = static_cast<const float *>(r.qx) + b0;
+        it.qy = static_cast<const float *>(r.qy) + b0;
+        it.out = static_cast<float *>(r.out) + b0;
+        it.out_alpha = r.out_alpha ? r.out_alpha + b0 : nullptr;
+        auto stage_in = [&](const float *src, const float **dst) {
             std::memcpy(hp, src, bytes);
             ok &= cudaMemcpyAsync(dp, hp, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
             *dst = reinterpret_cast<const float *>(dp);
             hp += b;
             dp += b;
         };
-        auto stage_out = [&](void *user, float **dst) {
+        auto stage_out = [&](float *user, float **dst) {
             *dst = reinterpret_cast<float *>(dp);
             f.copy_out.push_back({user, hp, bytes});
             hp += b;
             dp += b;
         };
         if (r.host_qx)
-            stage_in(r.qx, &it.qx);
+            stage_in(it.qx, &it.qx);
         if (r.host_qy)
-            stage_in(r.qy, &it.qy);
+            stage_in(it.qy, &it.qy);
         if (r.host_out)
-            stage_out(r.out, &it.out);
+            stage_out(it.out, &it.out);
         if (r.host_alpha)
-            stage_out(r.out_alpha, &it.out_alpha);
+            stage_out(it.out_alpha, &it.out_alpha);
     }
     if (!ok) {
         ctx_free(ctx, dstage, dev_bytes, st);
@@ -231,7 +287,8 @@ int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &r
         char *h = static_cast<char *>(f.pinned);
         for (size_t i = 0; i < rq.size(); ++i) {
             const Request &r = *rq[i];
-            const size_t bytes = 4 * static_cast<size_t>(r.m), b = align256(bytes);
+            const size_t bytes = 4 * static_cast<size_t>(pc[i].end - pc[i].begin);
+            const size_t b = align256(bytes);
             if (r.host_qx)
                 d += b, h += b;
             if (r.host_qy)
@@ -275,31 +332,37 @@ void worker_main(ServingRuntime *rt)
             for (const Flight::CopyOut &c : f.copy_out)
                 std::memcpy(c.dst, c.src, c.bytes);
             f.copy_out.clear();
-            finish(rt, f.ids, status);
+            finish_pieces(rt, f.pieces, status);
             rt->in_flight -= f.footprint;
             f.footprint = 0;
-            f.ids.clear();
+            f.pieces.clear();
             f.busy = false;
             rt->cv_done.notify_all();
         }
         if (rt->stop && rt->queue.empty() && !any_busy)
             break;
-        // 2. Admission into every free slot.
+        // 2. Admission into every free slot: one chunk of each queued request at most, in
+        // arrival order.
         for (Flight &f : rt->flights) {
             if (f.busy || rt->queue.empty())
                 continue;
-            std::vector<int64_t> ids;
+            std::vector<Piece> pieces;
             std::vector<Request *> rq;
             size_t fp = 0;
-            while (!rt->queue.empty()) {
-                const int64_t id = rt->queue.front();
+            double fpairs = 0.0;
+            for (size_t qi = 0; qi < rt->queue.size();) {
+                const int64_t id = rt->queue[qi];
                 Request &r = rt->reqs[id];
+                const int64_t b = static_cast<int64_t>(r.next_chunk) * r.chunk_m;
+                const int64_t e = std::min<int64_t>(b + r.chunk_m, r.m);
+                const double pairs = static_cast<double>(e - b) * static_cast<double>(r.n);
                 const Admit a = admission_step(r.solo, r.footprint, rt->budget, rt->in_flight, fp,
-                                               ids.size(), rt->max_items);
+                                               pieces.size(), rt->max_items, pairs, fpairs,
+                                               kFlightPairs);
                 if (a == Admit::kStop)
-                    break;  // the head waits for the next flight or for memory to free up
+                    break;  // the rest waits for the next flight or for memory to free up
                 if (a == Admit::kSolo) {
-                    rt->queue.pop_front();
+                    rt->queue.erase(rt->queue.begin() + static_cast<std::ptrdiff_t>(qi));
                     g.unlock();
                     int rc = interpolate_impl(rt->ctx, r.ds, r.qx, r.qy, r.m, &r.p, r.out,
                                               r.out_alpha, r.out_knn, f.stream, 0, 0);
@@ -312,37 +375,42 @@ void worker_main(ServingRuntime *rt)
                     continue;
                 }
                 if (a == Admit::kRejectOom) {
-                    rt->queue.pop_front();
+                    rt->queue.erase(rt->queue.begin() + static_cast<std::ptrdiff_t>(qi));
                     finish(rt, {id}, AIDW_ERR_OOM);
                     rt->cv_done.notify_all();
                     continue;
                 }
-                rt->queue.pop_front();
-                ids.push_back(id);
+                pieces.push_back({id, b, e});
                 rq.push_back(&r);
                 fp += r.footprint;
+                fpairs += pairs;
+                if (++r.next_chunk == r.nchunks) {
+                    rt->queue.erase(rt->queue.begin() + static_cast<std::ptrdiff_t>(qi));
+                    ++rt->stats.batched_requests;
+                } else {
+                    ++qi;
+                }
             }
-            if (ids.empty())
+            if (pieces.empty())
                 continue;
             f.busy = true;
-            f.ids = ids;
+            f.pieces = pieces;
             f.footprint = fp;
             rt->in_flight += fp;
             ++rt->stats.launches;
-            rt->stats.batched_requests += ids.size();
             int live = 0;
             for (const Flight &o : rt->flights)
                 live += o.busy ? 1 : 0;
             if (live > rt->stats.max_concurrent_launches)
                 rt->stats.max_concurrent_launches = live;
             g.unlock();
-            const int rc = launch_flight(rt, f, rq);
+            const int rc = launch_flight(rt, f, rq, pieces);
             g.lock();
             if (rc != AIDW_OK) {
-                finish(rt, f.ids, rc);
+                finish_pieces(rt, f.pieces, rc);
                 rt->in_flight -= f.footprint;
                 f.footprint = 0;
-                f.ids.clear();
+                f.pieces.clear();
                 f.busy = false;
                 f.copy_out.clear();
                 rt->cv_done.notify_all();
@@ -415,26 +483,31 @@ using namespace aidw;
 extern "C" {
 
 // Test hook (not in the public header): runs the serving runtime's admission of one flight over
-// a queue of `count` requests (solo flags, device footprints) against `budget` with `in_flight`
-// bytes already running, and writes each request's action: 0 taken into the flight, 1 run alone,
-// 2 failed with OOM, 3 left in the queue. Host only.
+// a queue of `count` chunks, one per queued request (solo flags, device footprints, nullable
+// pair-evaluations) against `budget` with `in_flight` bytes already running and a flight work
+// cap of max_flight_pairs (0: none), and writes each chunk's action: 0 taken into the flight,
+// 1 run alone, 2 failed with OOM, 3 left in the queue. Host only.
 int aidw_debug_admission(int64_t count, const int32_t *solo, const uint64_t *footprint,
-                         uint64_t budget, uint64_t in_flight, int32_t max_items, int32_t *action)
+                         uint64_t budget, uint64_t in_flight, int32_t max_items,
+                         const double *pairs, double max_flight_pairs, int32_t *action)
 {
     if (count < 0 || max_items < 1 || (count > 0 && (!solo || !footprint || !action)))
         return AIDW_ERR_INVALID_ARG;
     size_t fp = 0, n = 0;
+    double fpairs = 0.0;
     bool stopped = false;
     for (int64_t i = 0; i < count; ++i) {
         if (stopped) {
             action[i] = 3;
             continue;
         }
-        switch (admission_step(solo[i] != 0, footprint[i], budget, in_flight, fp, n,
-                               max_items)) {
+        const double pr = pairs ? pairs[i] : 0.0;
+        switch (admission_step(solo[i] != 0, footprint[i], budget, in_flight, fp, n, max_items,
+                               pr, fpairs, max_flight_pairs)) {
         case Admit::kTake:
             action[i] = 0;
             fp += footprint[i];
+            fpairs += pr;
             ++n;
             break;
         case Admit::kSolo:
@@ -561,7 +634,18 @@ int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, 
                 return AIDW_ERR_INVALID_ARG;
         }
     }
-    r.footprint = request_footprint(r, dev.n_pad, rt->cfg);
+    r.n = dev.n;
+    r.n_pad = dev.n_pad;
+    r.chunk_m = m;
+    if (!r.solo && m > 0) {
+        // Chunks of whole 256-query blocks, about kChunkPairs pair-evaluations each.
+        const double per = std::floor(kChunkPairs / static_cast<double>(dev.n) / 256.0) * 256.0;
+        r.chunk_m = std::max<int64_t>(256, static_cast<int64_t>(std::min(per, 1e15)));
+        if (r.chunk_m >= m)
+            r.chunk_m = m;
+        r.nchunks = static_cast<int32_t>((m + r.chunk_m - 1) / r.chunk_m);
+    }
+    r.footprint = request_footprint(r, r.chunk_m, dev.n_pad, rt->cfg);
     {
         std::lock_guard<std::mutex> g(rt->mu);
         if (rt->queue.size() >= rt->max_queue) {

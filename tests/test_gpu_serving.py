@@ -254,3 +254,40 @@ def test_backpressure_queue_full_then_resubmit():
         assert ctx.serving_stats().rejected_again == again
         with pytest.raises(aidw.AidwError):
             ctx.serving_set_queue_limit(0)
+
+
+def test_large_request_served_in_chunks():
+    """A request of 250,000 queries against 400,000 points (1e11 pair-evaluations) is cut into
+    three chunks of whole query blocks served by separate launches, and a small request
+    submitted after it rides in one of the first launches, so it completes first. The large
+    request's result matches the oracle on sampled queries and is bit-identical to the same
+    request served alone (the cut depends on its own sizes only)."""
+    import torch
+    with aidw.Context(0) as ctx:
+        big = workloads.small_case(61, 400000, 250000, k=10, pattern="clustered", side=800.0)
+        ds = ctx.create_dataset(big.x, big.y, big.z, big.area)
+        small = workloads.small_case(62, 5000, 2000, k=10, pattern="uniform", side=800.0)
+        ds2 = ctx.create_dataset(small.x, small.y, small.z, small.area)
+        p = aidw.default_params(k=10)
+        qx = torch.as_tensor(big.qx, dtype=torch.float32, device="cuda")
+        qy = torch.as_tensor(big.qy, dtype=torch.float32, device="cuda")
+        out_alone = torch.full((big.m,), float("nan"), dtype=torch.float32, device="cuda")
+        rc, rid = ctx.submit(ds, qx, qy, p, out_alone)
+        assert rc == aidw.OK and ctx.wait(rid, 120_000_000) == aidw.OK
+        launches0 = ctx.serving_stats().launches
+        assert launches0 >= 3, "the large request should take three launches"
+        out_mix = torch.full_like(out_alone, float("nan"))
+        sq = small.qx.astype(np.float32), small.qy.astype(np.float32)
+        out_small = np.full(small.m, np.nan, dtype=np.float32)
+        rc, rbig = ctx.submit(ds, qx, qy, p, out_mix)
+        rc2, rsmall = ctx.submit(ds2, sq[0], sq[1], p, out_small)
+        assert rc == aidw.OK and rc2 == aidw.OK
+        assert ctx.wait(rbig, 120_000_000) == aidw.OK and ctx.wait(rsmall, 60_000_000) == aidw.OK
+        assert ctx.latency_us(rsmall) < ctx.latency_us(rbig)
+        torch.cuda.synchronize()
+        assert torch.equal(out_alone, out_mix)
+        idx = np.random.default_rng(3).choice(big.m, 512, replace=False)
+        ref, _ = oracle_for(big, aidw.F32C, q_idx=idx)
+        assert rel_err(out_mix.cpu().numpy()[idx], ref).max() <= TOL_F32
+        ref_s, _ = oracle_for(small, aidw.F32C)
+        assert rel_err(out_small, ref_s).max() <= TOL_F32
