@@ -291,3 +291,13 @@ def test_large_request_served_in_chunks():
         assert rel_err(out_mix.cpu().numpy()[idx], ref).max() <= TOL_F32
         ref_s, _ = oracle_for(small, aidw.F32C)
         assert rel_err(out_small, ref_s).max() <= TOL_F32
+        # The same request from host arrays with the alpha output: every chunk is staged and
+        # written back at its own offset.
+        hx, hy = big.qx.astype(np.float32), big.qy.astype(np.float32)
+        hout = np.full(big.m, np.nan, dtype=np.float32)
+        halpha = np.full(big.m, np.nan, dtype=np.float32)
+        rc, rh = ctx.submit(ds, hx, hy, p, hout, out_alpha=halpha)
+        assert rc == aidw.OK and ctx.wait(rh, 120_000_000) == aidw.OK
+        assert np.array_equal(hout, out_alone.cpu().numpy())
+        assert np.all(np.isfinite(halpha))
+        assert np.abs(halpha[idx] - ref["alpha"]).max() <= 1e-5
