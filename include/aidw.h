@@ -311,8 +311,10 @@ int aidw_tune_cache_load(const char *path);
  * serving thread, started on first use, admits queued requests in arrival order while their
  * device footprint fits the serving budget and packs them into persistent batch launches
  * (continuous batching: a new launch starts on another stream while earlier ones still run).
- * An FP32 request's result does not depend on what it was batched with. FP64 requests and
- * requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests
+ * A large FP32 request is cut into chunks of whole 256-query blocks served by successive
+ * launches, one chunk per queued request per launch, and small requests may also take an
+ * express launch slot out of arrival order. An FP32 request's result does not depend on what
+ * it was batched with. FP64 requests and requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests
  * unless configured otherwise) is full: the request was not accepted, and the caller resubmits
  * later or sheds it; a request larger than the whole budget finishes with AIDW_ERR_OOM. */
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,

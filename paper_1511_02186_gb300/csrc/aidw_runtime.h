@@ -103,8 +103,9 @@ struct BatchState {
     void *sort_tmp = nullptr;
     aidw_tune_config cfg{};  // shape the batch was built with
 };
+// reserve_ctas_per_sm: persistent CTAs per SM to leave free (for a concurrent launch).
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
-                BatchState *bs, const aidw_tune_config &cfg);
+                BatchState *bs, const aidw_tune_config &cfg, int reserve_ctas_per_sm = 0);
 int batch_enqueue(aidw_ctx *ctx, const BatchState &bs, cudaStream_t st);
 void batch_release(aidw_ctx *ctx, BatchState *bs, cudaStream_t st);
 // Device bytes one batch item of m queries against n_pad points with k neighbours needs.

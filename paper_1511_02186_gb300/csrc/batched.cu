@@ -413,8 +413,9 @@ BatchKernel batch_kernel_for(int qw, bool lean)
 // Shape field unit_order = 1: every kBatchP1Every-th persistent CTA takes phase-1 units first.
 constexpr int kBatchP1Every = 4;
 
-// Persistent grid: CTAs per SM as occupancy allows, or fewer if the shape asks for it.
-int batch_grid(int sm_count, size_t dyn, int qw, bool lean, int ctas_per_sm)
+// Persistent grid: CTAs per SM as occupancy allows, or fewer if the shape asks for it, less
+// `reserve` per SM (left free for another launch; at least one CTA per SM remains).
+int batch_grid(int sm_count, size_t dyn, int qw, bool lean, int ctas_per_sm, int reserve)
 {
     const BatchKernel fn = batch_kernel_for(qw, lean);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
@@ -423,6 +424,7 @@ int batch_grid(int sm_count, size_t dyn, int qw, bool lean, int ctas_per_sm)
     n = n > 0 ? n : 1;
     if (ctas_per_sm > 0 && ctas_per_sm < n)
         n = ctas_per_sm;
+    n = n - reserve > 0 ? n - reserve : 1;
     return n * sm_count;
 }
 
@@ -497,7 +499,7 @@ size_t batch_item_bytes(int64_t n_pad, int64_t m, int k, const aidw_tune_config 
 
 // Validates the items and builds the device tables of a batch in library memory.
 int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cudaStream_t st,
-                BatchState *bs, const aidw_tune_config &cfg)
+                BatchState *bs, const aidw_tune_config &cfg, int reserve_ctas_per_sm)
 {
     if (!tune_valid(cfg))
         return AIDW_ERR_INVALID_ARG;
@@ -658,7 +660,7 @@ int batch_build(aidw_ctx *ctx, const aidw_batch_item *items, int32_t count, cuda
     bs->cfg = cfg;
     bs->lean = lean;
     bs->grid = batch_grid(ctx_sm_count(ctx), bs->dyn_smem, cfg.queries_per_thread, lean,
-                          cfg.ctas_per_sm);
+                          cfg.ctas_per_sm, reserve_ctas_per_sm);
     bool ok = true;
     if (count > 0)
         ok &= cudaMemcpyAsync(bs->d_items, h.data(), sizeof(BatchItemDev) * count,

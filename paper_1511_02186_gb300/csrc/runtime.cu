@@ -51,6 +51,15 @@ inline size_t align256(size_t b)
 constexpr double kChunkPairs = 4e10;
 constexpr double kFlightPairs = 1e11;
 
+// Express lane: requests of at most kExpressPairs pair-evaluations (about 1-2 ms on one CTA per
+// SM) may also go to a launch of their own, one persistent CTA per SM, taken out of arrival
+// order; the other launches leave one CTA slot per SM free for it, so that a small request
+// starts at once instead of waiting for a large launch to release the SMs (measured cost for a
+// large batch: 72.3 against 70.9 ms with 7 instead of 8 CTAs per SM).
+constexpr double kExpressPairs = 5e8;
+constexpr double kExpressFlightPairs = 2e9;
+constexpr size_t kExpressScan = 256;  // queued requests the express lane looks at
+
 struct Request {
     int64_t ds = 0;
     const void *qx = nullptr, *qy = nullptr;
@@ -79,6 +88,7 @@ struct Piece {
 
 struct Flight {
     bool busy = false;
+    bool express = false;  // the express lane (one persistent CTA per SM)
     std::vector<Piece> pieces;
     cudaEvent_t done_ev = nullptr;
     cudaStream_t stream = nullptr;
@@ -108,7 +118,8 @@ struct ServingRuntime {
     size_t budget = size_t(8) << 30;  // device bytes in flight
     size_t in_flight = 0;
     int max_items = 256;
-    int n_slots = 2;
+    int n_slots = 2;           // launches at once, besides the express lane
+    bool express_lane = true;  // flights.back() is the express lane
     std::vector<Flight> flights;
     bool stop = false;
     std::thread worker;
@@ -278,7 +289,14 @@ int launch_flight(ServingRuntime *rt, Flight &f, const std::vector<Request *> &r
         return AIDW_ERR_CUDA;
     }
     BatchState bs{};
-    rc = batch_build(ctx, items.data(), static_cast<int32_t>(items.size()), st, &bs, rt->cfg);
+    aidw_tune_config cfg = rt->cfg;
+    int reserve = 0;
+    if (f.express)
+        cfg.ctas_per_sm = 1;
+    else if (rt->express_lane)
+        reserve = 1;
+    rc = batch_build(ctx, items.data(), static_cast<int32_t>(items.size()), st, &bs, cfg,
+                     reserve);
     if (rc == AIDW_OK)
         rc = batch_enqueue(ctx, bs, st);
     if (rc == AIDW_OK) {
@@ -350,7 +368,29 @@ void worker_main(ServingRuntime *rt)
             std::vector<Request *> rq;
             size_t fp = 0;
             double fpairs = 0.0;
-            for (size_t qi = 0; qi < rt->queue.size();) {
+            if (f.express) {
+                // Small whole requests from the first kExpressScan queued, out of order.
+                for (size_t qi = 0; qi < rt->queue.size() && qi < kExpressScan;) {
+                    const int64_t id = rt->queue[qi];
+                    Request &r = rt->reqs[id];
+                    const double pairs = static_cast<double>(r.m) * static_cast<double>(r.n);
+                    const bool small = !r.solo && r.nchunks == 1 && pairs <= kExpressPairs;
+                    if (!small || admission_step(false, r.footprint, rt->budget, rt->in_flight,
+                                                 fp, pieces.size(), rt->max_items, pairs,
+                                                 fpairs, kExpressFlightPairs) != Admit::kTake) {
+                        ++qi;
+                        continue;
+                    }
+                    rt->queue.erase(rt->queue.begin() + static_cast<std::ptrdiff_t>(qi));
+                    pieces.push_back({id, 0, r.m});
+                    rq.push_back(&r);
+                    fp += r.footprint;
+                    fpairs += pairs;
+                    r.next_chunk = 1;
+                    ++rt->stats.batched_requests;
+                }
+            }
+            for (size_t qi = 0; !f.express && qi < rt->queue.size();) {
                 const int64_t id = rt->queue[qi];
                 Request &r = rt->reqs[id];
                 const int64_t b = static_cast<int64_t>(r.next_chunk) * r.chunk_m;
@@ -426,6 +466,18 @@ void worker_main(ServingRuntime *rt)
     }
 }
 
+// The launch slots: n_slots regular ones, then the express lane.
+void create_flights(ServingRuntime *rt)
+{
+    rt->flights.resize(rt->n_slots + (rt->express_lane ? 1 : 0));
+    for (Flight &f : rt->flights) {
+        cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming);
+    }
+    if (rt->express_lane)
+        rt->flights.back().express = true;
+}
+
 ServingRuntime *ensure_serving(aidw_ctx *ctx)
 {
     const size_t left = ctx_budget_left(ctx);
@@ -440,11 +492,7 @@ ServingRuntime *ensure_serving(aidw_ctx *ctx)
         if (left != SIZE_MAX)
             rt->budget = left / 2;
         cudaSetDevice(ctx_device(ctx));
-        rt->flights.resize(rt->n_slots);
-        for (Flight &f : rt->flights) {
-            cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
-            cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming);
-        }
+        create_flights(rt);
         rt->worker = std::thread(worker_main, rt);
     }
     return rt;
@@ -553,11 +601,7 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
         if (streams)
             rt->n_slots = streams;
         cudaSetDevice(ctx_device(ctx));
-        rt->flights.resize(rt->n_slots);
-        for (Flight &f : rt->flights) {
-            cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking);
-            cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming);
-        }
+        create_flights(rt);
         ctx_serving(ctx) = rt;
     }
     rt->worker = std::thread(worker_main, rt);
