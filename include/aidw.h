@@ -151,11 +151,12 @@ int aidw_idw(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int
  * (or runs with CUDA_MODULE_LOADING=EAGER).
  *   qx, qy, out  DEVICE arrays of m floats on the context's device (host arrays are rejected)
  *   p            as for aidw_interpolate; p->precision must be AIDW_F32C
- * Phase 1 takes aidw_interpolate's pruned route (queries put in Z-order, nearest data tiles
- * first) when aidw_interpolate would and its scratch, about m * (4k + 49) bytes, fits the array
- * (m up to about 189,000 at k = 10); otherwise it scans every (query, data point) pair in data
- * splits, which for many queries costs far more (at 131,072 queries x 1M points about 61 ms
- * against 3.4 ms for the pruned scan; phase 2 is the same either way). Limit: the split scan
+ * Phase 1 takes aidw_interpolate's route when its scratch fits the array: up to 32,768 queries
+ * one warp per query (about m * (4k + 24) bytes), above that the pruned scan over queries put
+ * in Z-order (about m * (4k + 49) bytes, m up to about 189,000 at k = 10); otherwise it scans
+ * every (query, data point) pair in data splits, which for many queries costs far more (at
+ * 131,072 queries x 1M points about 61 ms against 3.4 ms for the pruned scan; phase 2 is the
+ * same either way). Limit: the split scan
  * needs about m * (4k + 24) bytes within 16 MiB (m <= 262,144 for k = 10, about 110,000 for
  * k = 32); larger calls return AIDW_ERR_INVALID_ARG. All calls share the one array and it keeps
  * the last call's contents (every element a call reads, it has written first): calls whose

@@ -490,6 +490,24 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
            static_cast<double>(m) >= need;
 }
 
+// Whether an FP32 call takes the per-query phase 1 (one warp per query). Its cost grows with
+// the query count alone (about 25 ns of the GPU per query against 1M points, 13 ns against
+// 65,536), while the block scans share their tiles among a block's queries and gain as the
+// queries get denser. Measured phase 1 (ms, against 1M uniform points / 65,536 clustered
+// points; block scans = the split scan below 12,600 queries, the pruned scan above):
+//   queries        1,024   4,096   8,192   32,768   131,072
+//   block scans    2.63    3.41    4.46    1.93     1.09     /  0.61  0.64  0.73  0.54  0.46
+//   warp per query 0.24    0.25    0.34    0.99     3.24     /  0.13  0.14  0.19  0.49  1.67
+// so calls of up to kWarpKnnMaxQueries take it.
+constexpr int64_t kWarpKnnMaxQueries = 32768;
+
+bool use_warp_knn(const DatasetDev &ds, int64_t m, int sm_count)
+{
+    (void)ds;
+    (void)sm_count;
+    return m <= kWarpKnnMaxQueries;
+}
+
 void plan_culled_knn(Plan *pl, int64_t n_pad)
 {
     pl->knn.splits = 1;
@@ -576,6 +594,36 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
     return AIDW_OK;
 }
 
+// FP32 interpolation with the per-query (one warp per query) phase 1, in the caller's order:
+// phase 1, selection, phase 2, finalisation (four launches, no query ordering).
+int enqueue_warp(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
+                 const aidw_params &p, const float *qx, const float *qy, const Scratch &sc,
+                 float *out, float *out_alpha, int32_t *out_knn, cudaStream_t st, bool profile)
+{
+    PhaseMarks marks(ctx, st, profile);
+    marks.at(0);
+    bool ok = launch_f32_knn_warp(ds, pl.m, qx, qy, p.k, sc, ctx->sm_count, st) == cudaSuccess;
+    marks.at(1);
+    ok = ok && launch_f32_select(pl, p.k, r_exp, alpha_map(p), sc, out_alpha, out_knn, st) ==
+                   cudaSuccess;
+    marks.at(2);
+    ok = ok && launch_f32_weights(ds, pl, qx, qy, sc, ctx->d_err, st) == cudaSuccess;
+    marks.at(3);
+    ok = ok && launch_f32_finalize(pl, sc, out, st) == cudaSuccess;
+    if (!ok)
+        return AIDW_ERR_CUDA;
+    marks.at(4);
+    if (profile) {
+        ctx->last = aidw_kernel_times{};
+        ctx->last.splits = 1;
+        ctx->last.query_blocks = 0;
+        ctx->last.launches = 4;
+        ctx->last.weight_splits = pl.w.splits;
+        ctx->last_valid = true;
+    }
+    return AIDW_OK;
+}
+
 // Reads and clears the on-device error word (synchronous).
 int consume_device_error(aidw_ctx *ctx, cudaStream_t st)
 {
@@ -635,12 +683,21 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         }
     }
 
+    // force_knn_splits < 0 (tests): the per-query phase 1 whatever the sizes.
+    const bool warp = p->precision == AIDW_F32C &&
+                      (force_knn_splits < 0 ||
+                       (force_knn_splits == 0 && use_warp_knn(ds, m, ctx->sm_count)));
     Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
-                        force_knn_splits, force_w_splits, cfg);
-    const bool cull =
-        force_knn_splits == 0 && use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl);
+                        force_knn_splits > 0 ? force_knn_splits : 0, force_w_splits, cfg);
+    const bool cull = !warp && force_knn_splits == 0 &&
+                      use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl);
     if (cull)
         plan_culled_knn(&pl, ds.n_pad);
+    if (warp) {
+        // One list per query, [k][m], for the selection kernel.
+        pl.knn.splits = 1;
+        pl.knn.split_len = ds.n_pad;
+    }
     const size_t sb = scratch_bytes(p->precision, pl, p->k) +
                       (cull ? culled_extra_bytes(m, p->precision) : 0);
     // Staging for host arrays.
@@ -688,10 +745,13 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         ctx_free(ctx, blk, total, st);
         return AIDW_ERR_CUDA;
     }
-    rc = cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, extra, dout, dalpha, dknn,
-                               st, ctx->profiling)
-              : enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn,
-                                      st, ctx->profiling);
+    rc = warp   ? enqueue_warp(ctx, ds, r_exp, pl, *p, static_cast<const float *>(dqx),
+                               static_cast<const float *>(dqy), sc, static_cast<float *>(dout),
+                               dalpha, dknn, st, ctx->profiling)
+         : cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, extra, dout, dalpha, dknn,
+                                 st, ctx->profiling)
+                : enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn,
+                                        st, ctx->profiling);
     if (rc == AIDW_OK && host_any) {
         ok = true;
         if (ko == 0)
@@ -845,10 +905,12 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     const size_t np = static_cast<size_t>(n_pad);
     const int64_t ntiles = n_pad / kTileF32Knn;
     const int64_t nsub = n_pad / kSubTile;
+    const int64_t nsuper = (ntiles + kSuperTiles - 1) / kSuperTiles;
     const size_t bytes = align256(np * sizeof(float4)) + align256(np * sizeof(float2)) +
                          align256(np * sizeof(int32_t)) + align256(np * sizeof(double2)) +
                          align256(np * sizeof(double)) + align256(ntiles * sizeof(float4)) +
-                         align256(nsub * sizeof(float4)) + align256(sizeof(float4));
+                         align256(nsub * sizeof(float4)) + align256(nsuper * sizeof(float4)) +
+                         align256(sizeof(float4));
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         if (ctx->fail_after >= 0) {
@@ -930,6 +992,8 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     b += align256(ntiles * sizeof(float4));
     float4 *sbox = reinterpret_cast<float4 *>(b);
     b += align256(nsub * sizeof(float4));
+    float4 *upbox = reinterpret_cast<float4 *>(b);
+    b += align256(nsuper * sizeof(float4));
     float4 *box = reinterpret_cast<float4 *>(b);
 
     int rc = AIDW_OK;
@@ -963,6 +1027,7 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
         }
         ok = ok && tile_boxes(nxy2, ntiles, tbox, 0) == cudaSuccess;
         ok = ok && sub_tile_boxes(nxy2, nsub, sbox, 0) == cudaSuccess;
+        ok = ok && super_tile_boxes(tbox, ntiles, nsuper, upbox, 0) == cudaSuccess;
         ok = ok && cudaDeviceSynchronize() == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -981,6 +1046,7 @@ int aidw_create_dataset(aidw_ctx *ctx, const void *x, const void *y, const void 
     rec.dev.orig = orig;
     rec.dev.tile_box = tbox;
     rec.dev.sub_box = sbox;
+    rec.dev.super_box = upbox;
     rec.dev.box = box;
     rec.dev.xy64 = xy64;
     rec.dev.z64 = z64;

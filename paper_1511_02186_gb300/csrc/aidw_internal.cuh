@@ -18,6 +18,7 @@ constexpr int kTileF64Knn = 512;   // double2 (x, y): 8 KiB per buffer
 constexpr int kTileF64W = 512;     // double2 + double: 12 KiB per buffer
 constexpr int kPadPoints = 2048;   // common multiple of every tile and split granule
 constexpr int kSubTile = 64;       // points per sub-tile box (pruned phase 1)
+constexpr int kSuperTiles = 32;    // tiles per super-tile box (the per-query phase 1)
 
 // Added under the square of distances: it is absorbed (below half an ulp) for any distance
 // above ~1e-15 of unit scale, and turns an exact coincidence (d2 == 0) into d2 == kEps so
@@ -58,6 +59,7 @@ struct DatasetDev {
     const int32_t *orig;    // [n_pad] caller's index of each stored point, -1 for padding
     const float4 *tile_box; // [n_pad / kTileF32Knn] (xmin, ymin, xmax, ymax) of finite points
     const float4 *sub_box;  // [n_pad / kSubTile] the same per 64-point sub-tile
+    const float4 *super_box; // [ceil(tiles / kSuperTiles)] the same per 32 tiles
     const float4 *box;      // [1] bounding box of all points
     const double2 *xy64;    // [n_pad] caller's order
     const double *z64;      // [n_pad] caller's order
@@ -129,6 +131,11 @@ cudaError_t launch_f32_weights(const DatasetDev &ds, const Plan &pl, const float
                                const float *qy, const Scratch &sc, int *err, cudaStream_t st);
 cudaError_t launch_f32_finalize(const Plan &pl, const Scratch &sc, float *out,
                                 cudaStream_t st, const uint32_t *perm = nullptr);
+// Phase 1 with one warp per query, in the caller's order (queries that lie far apart compared
+// with the data points): one split's lists in sc.part_d2 (and sc.part_idx when non-null).
+cudaError_t launch_f32_knn_warp(const DatasetDev &ds, int64_t m, const float *qx,
+                                const float *qy, int k, const Scratch &sc, int sm_count,
+                                cudaStream_t st);
 // Phase 1 over Z-ordered queries with nearest-first tile visiting and bounding-box pruning
 // (one split); sqx / sqy are the queries in Z-order.
 constexpr int64_t kMaxCullTiles = 8192;
@@ -147,6 +154,9 @@ cudaError_t morton_keys(const float *x, const float *y, const float2 *xy, int64_
                         cudaStream_t st);
 cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaStream_t st);
 cudaError_t sub_tile_boxes(const float4 *nxy2, int64_t nsub, float4 *boxes, cudaStream_t st);
+// Box of every group of kSuperTiles consecutive tile boxes (the last group may be shorter).
+cudaError_t super_tile_boxes(const float4 *tile_boxes, int64_t ntiles, int64_t nsuper,
+                             float4 *boxes, cudaStream_t st);
 cudaError_t gather_queries(const float *qx, const float *qy, const uint32_t *perm, int64_t m,
                            float *sqx, float *sqy, cudaStream_t st);
 cudaError_t morton_keys_f64(const double *x, const double *y, int64_t n, const float4 *box,

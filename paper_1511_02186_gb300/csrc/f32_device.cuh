@@ -346,6 +346,194 @@ static __device__ __noinline__ void fused_select_query(const float *d, int k,
         fs->out_alpha[fs->perm[q]] = static_cast<float>(alpha);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Phase 1 with one warp per query. A block of queries scans the data tiles near all of its
+// queries together (knn_cull_unit); when the queries lie far apart compared with the data points
+// (few queries, or many fewer queries than points) the block shares little, its warps scan the
+// union of what each query needs, and a call with few queries leaves most SMs idle. Here a warp
+// serves one query at a time: its 32 lanes hold the 32 smallest squared distances seen so far
+// as a list sorted across the lanes (lane j the j-th smallest, with the point's stored
+// position), scan 32 points per step with one point per lane, and take the points closer than
+// the k-th entry: a few by shifting the larger entries up one lane each, more by a bitonic sort
+// of the step's candidates and a bitonic merge with the list.
+// The points are visited through the dataset's box hierarchy (32-tile super-tiles, 512-point
+// tiles, 64-point sub-tiles), nearest box first at every level, skipping every box whose bound
+// exceeds the current k-th distance. The bounds are shrunk by 2^-20 for rounding as in
+// knn_cull_unit, so no skipped point could enter the list: the k smallest values are those of a
+// full scan. k <= 32.
+// ---------------------------------------------------------------------------------------------
+constexpr unsigned kFullMask = 0xffffffffu;
+// Up to this many candidates in a step are inserted one at a time; more are sorted and merged.
+constexpr int kWarpInsertMax = 6;
+
+// Squared-distance lower bound from (qx, qy) to a box (xmin, ymin, xmax, ymax), shrunk for
+// rounding; +inf for an empty box.
+__device__ __forceinline__ float box_bound(float qx, float qy, float4 b)
+{
+    const float dx = fmaxf(0.0f, fmaxf(b.x - qx, qx - b.z));
+    const float dy = fmaxf(0.0f, fmaxf(b.y - qy, qy - b.w));
+    return __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), kBoundShrink);
+}
+
+// Compare-exchange of a bitonic network across lanes: in an ascending run (up) the lower lane
+// of each pair keeps the smaller entry. Equal entries stay where they are.
+__device__ __forceinline__ void warp_cx(float &v, int32_t &i, int stride, bool up)
+{
+    const float ov = __shfl_xor_sync(kFullMask, v, stride);
+    const int32_t oi = __shfl_xor_sync(kFullMask, i, stride);
+    const bool lower = (threadIdx.x & stride) == 0;
+    const bool take = (lower == up) ? (ov < v) : (ov > v);
+    if (take) {
+        v = ov;
+        i = oi;
+    }
+}
+
+// Points [p, p + 32) of the Z-ordered copy, one per lane, against the warp's list (ld, li) and
+// its k-th entry thr (warp-uniform, updated).
+__device__ __forceinline__ void warp_scan32(const float4 *__restrict__ nxy2, int64_t p, float qx,
+                                            float qy, int k, float &ld, int32_t &li, float &thr)
+{
+    const int lane = threadIdx.x & 31;
+    const float4 pt = nxy2[p + lane];
+    const float d = dist2_neg(qx, qy, pt.x, pt.z);
+    unsigned cand = __ballot_sync(kFullMask, d < thr);
+    if (!cand)
+        return;
+    if (__popc(cand) <= kWarpInsertMax) {
+        // Few candidates: each is inserted in turn by shifting the larger entries up one lane.
+        while (cand) {
+            const int src = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const float c = __shfl_sync(kFullMask, d, src);
+            if (!(c < thr))
+                continue;
+            const int32_t ci = static_cast<int32_t>(p + src);
+            const float up = __shfl_up_sync(kFullMask, ld, 1);
+            const int32_t upi = __shfl_up_sync(kFullMask, li, 1);
+            if (!(ld <= c)) {
+                const bool here = lane == 0 || up <= c;
+                ld = here ? c : up;
+                li = here ? ci : upi;
+            }
+            thr = __shfl_sync(kFullMask, ld, k - 1);
+        }
+        return;
+    }
+    const bool is_cand = (cand >> lane) & 1u;
+    float v = is_cand ? d : CUDART_INF_F;
+    int32_t vi = is_cand ? static_cast<int32_t>(p + lane) : -1;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+            warp_cx(v, vi, stride, (lane & size) == 0);
+    }
+    // The 32 smallest of the two sorted lists, as a bitonic sequence, then sorted.
+    const float rv = __shfl_sync(kFullMask, v, 31 - lane);
+    const int32_t ri = __shfl_sync(kFullMask, vi, 31 - lane);
+    if (rv < ld) {
+        ld = rv;
+        li = ri;
+    }
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1)
+        warp_cx(ld, li, stride, true);
+    thr = __shfl_sync(kFullMask, ld, k - 1);
+}
+
+// Visit key of a box: its bound (the high 32 bits, so keys order by bound) and, below, the
+// distance from the query to the box centre (so that among boxes the query lies in, bound 0,
+// the one centred nearest comes first), the low 5 bits left for the lane. ~0 for an empty box.
+__device__ __forceinline__ unsigned long long box_key(float qx, float qy, float4 b)
+{
+    const float lb = box_bound(qx, qy, b);
+    if (!(lb < CUDART_INF_F))
+        return ~0ull;
+    const float cx = 0.5f * (b.x + b.z) - qx, cy = 0.5f * (b.y + b.w) - qy;
+    const float cd = fminf(fmaf(cx, cx, cy * cy), 3.0e38f);
+    return (static_cast<unsigned long long>(__float_as_uint(lb)) << 32) |
+           (static_cast<unsigned long long>(__float_as_uint(cd) >> 5) << 5);
+}
+
+// The smallest of the lanes' keys with its lane in the low 5 bits; ~0 if all are ~0.
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long key)
+{
+    const int lane = threadIdx.x & 31;
+    if (key != ~0ull)
+        key |= static_cast<unsigned long long>(lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(kFullMask, key, o);
+        key = other < key ? other : key;
+    }
+    return key;
+}
+
+// Whether the box of a visit key may hold a point closer than thr (its bound does not exceed
+// thr); false for ~0.
+__device__ __forceinline__ bool key_open(unsigned long long key, float thr)
+{
+    return key != ~0ull && !(__uint_as_float(static_cast<uint32_t>(key >> 32)) > thr);
+}
+
+// The k nearest stored points of (qx, qy) by one warp: lanes 0..k-1 end holding the k smallest
+// squared distances in ascending order (ld) and the points' stored positions (li). Boxes are
+// visited depth first, the children of each box nearest first (super-tiles in groups of 32, a
+// super-tile's 32 tiles, a tile's 8 sub-tiles; by bound, then by centre distance), each while
+// its bound does not exceed the current k-th distance: the first sub-tiles scanned are the
+// nearest, so the k-th distance falls early and the rest is mostly pruned. Empty boxes are never
+// visited.
+__device__ __forceinline__ void warp_knn(const DatasetDev &ds, float qx, float qy, int k,
+                                         float &ld, int32_t &li)
+{
+    constexpr int S = kTileF32Knn / kSubTile;  // 8 sub-tiles
+    const int lane = threadIdx.x & 31;
+    const int64_t ntiles = ds.n_pad / kTileF32Knn;
+    const int64_t nsuper = (ntiles + kSuperTiles - 1) / kSuperTiles;
+    ld = CUDART_INF_F;
+    li = -1;
+    float thr = CUDART_INF_F;
+    for (int64_t b = 0; b < nsuper; b += 32) {
+        const int64_t s = b + lane;
+        unsigned long long ks = s < nsuper ? box_key(qx, qy, ds.super_box[s]) : ~0ull;
+        for (;;) {
+            const unsigned long long ms = warp_min_key(ks);
+            if (!key_open(ms, thr))
+                break;
+            const int js = static_cast<int>(ms & 31ull);
+            if (lane == js)
+                ks = ~0ull;
+            const int64_t t0 = (b + js) * kSuperTiles;
+            const int64_t t = t0 + lane;
+            unsigned long long kt = t < ntiles ? box_key(qx, qy, ds.tile_box[t]) : ~0ull;
+            for (;;) {
+                const unsigned long long mt = warp_min_key(kt);
+                if (!key_open(mt, thr))
+                    break;
+                const int jt = static_cast<int>(mt & 31ull);
+                if (lane == jt)
+                    kt = ~0ull;
+                const int64_t tt = t0 + jt;
+                unsigned long long ku =
+                    lane < S ? box_key(qx, qy, ds.sub_box[tt * S + lane]) : ~0ull;
+                for (;;) {
+                    const unsigned long long mu = warp_min_key(ku);
+                    if (!key_open(mu, thr))
+                        break;
+                    const int ju = static_cast<int>(mu & 31ull);
+                    if (lane == ju)
+                        ku = ~0ull;
+                    const int64_t p = tt * kTileF32Knn + static_cast<int64_t>(ju) * kSubTile;
+#pragma unroll
+                    for (int u = 0; u < kSubTile; u += 32)
+                        warp_scan32(ds.nxy2, p + u, qx, qy, k, ld, li, thr);
+                }
+            }
+        }
+    }
+}
+
 // Shared-memory scratch of a pruned phase-1 unit.
 struct CullShared {
     float red[4][kThreads / 32];

@@ -5,6 +5,8 @@
 //   f32_weights_kernel  grid (query blocks, data splits): phase-2 unit per CTA (weighted sums)
 //   f32_finalize_kernel one thread per query: split merge, Eq. 1 ratio in FP64
 // The unit bodies live in f32_device.cuh and are shared with the persistent batched kernel.
+#include <algorithm>
+
 #include "f32_device.cuh"
 
 namespace aidw {
@@ -39,6 +41,31 @@ f32_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q < m)
         select_query(q, m, S, k, r_exp, am, part_d2, part_idx, qp, out_alpha, out_knn, perm);
+}
+
+// Phase 1 with one warp per query (warp_knn), in the caller's order: each query's k nearest
+// squared distances (and stored positions mapped to caller indices when part_idx is non-null)
+// as one split's lists [k][m], for the selection kernel, which amortises its FP64 work over a
+// thread per query.
+__global__ void __launch_bounds__(kThreads)
+f32_knn_warp_kernel(DatasetDev ds, int64_t m, const float *__restrict__ qx,
+                    const float *__restrict__ qy, int k, float *__restrict__ part_d2,
+                    int32_t *__restrict__ part_idx)
+{
+    constexpr int W = kThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * W + (threadIdx.x >> 5); q < m;
+         q += nwarps) {
+        float ld;
+        int32_t li;
+        warp_knn(ds, qx[q], qy[q], k, ld, li);
+        if (lane < k) {
+            part_d2[static_cast<int64_t>(lane) * m + q] = ld;
+            if (part_idx)
+                part_idx[static_cast<int64_t>(lane) * m + q] = li >= 0 ? ds.orig[li] : -1;
+        }
+    }
 }
 
 template <int KP, int Q, bool IDX>
@@ -216,6 +243,20 @@ cudaError_t launch_f32_select(const Plan &pl, int k, double r_exp, const AlphaMa
         pl.m, pl.knn.splits, k, r_exp, am, static_cast<const float *>(sc.part_d2),
         pl.with_idx ? sc.part_idx : nullptr, static_cast<QParamF32 *>(sc.qparam), out_alpha,
         out_knn, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_knn_warp(const DatasetDev &ds, int64_t m, const float *qx,
+                                const float *qy, int k, const Scratch &sc, int sm_count,
+                                cudaStream_t st)
+{
+    constexpr int W = kThreads / 32;
+    const int64_t want = (m + W - 1) / W;
+    const int64_t cap = static_cast<int64_t>(sm_count) * 16;
+    const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min(want, cap)));
+    f32_knn_warp_kernel<<<grid, kThreads, 0, st>>>(ds, m, qx, qy, k,
+                                                   static_cast<float *>(sc.part_d2),
+                                                   sc.part_idx);
     return cudaGetLastError();
 }
 

@@ -15,10 +15,10 @@
 // this file's module, and with it the array, on the device, so it belongs at set-up and not in
 // the middle of a request.
 //
-// The call takes the same phase-1 route as aidw_interpolate when its scratch fits: with enough
-// queries, the pruned scan over Z-ordered queries (the query ordering needs about 24 more bytes
-// per query); otherwise, or when that does not fit, the split scan with as few splits as the
-// area requires.
+// The call takes the same phase-1 route as aidw_interpolate when its scratch fits: up to
+// 32,768 queries one warp per query; above, the pruned scan over Z-ordered queries (the query
+// ordering needs about 24 more bytes per query); otherwise, or when that does not fit, the split
+// scan with as few splits as the area requires.
 #include <mutex>
 
 #include "aidw_internal.cuh"
@@ -91,6 +91,24 @@ extern "C" int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const fl
         return AIDW_ERR_CUDA;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Plan planned = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, 0);
+
+    // Per-query phase 1 where aidw_interpolate would take it (one list per query, no ordering).
+    if (use_warp_knn(dev, m, 0)) {
+        Plan pl = planned;
+        pl.knn.splits = 1;
+        pl.knn.split_len = dev.n_pad;
+        while (scratch_bytes(AIDW_F32C, pl, p->k) > kNoAllocScratchBytes && pl.w.splits > 1) {
+            pl = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, pl.w.splits - 1);
+            pl.knn.splits = 1;
+            pl.knn.split_len = dev.n_pad;
+        }
+        if (scratch_bytes(AIDW_F32C, pl, p->k) <= kNoAllocScratchBytes) {
+            Scratch sc;
+            scratch_carve(base, AIDW_F32C, pl, p->k, &sc);
+            return enqueue_warp(ctx, dev, r_exp, pl, *p, qx, qy, sc, out, nullptr, nullptr, st,
+                                false);
+        }
+    }
 
     // Pruned phase 1 where aidw_interpolate would take it, with fewer phase-2 splits if the
     // area needs it (splits only regroup the FP32 partial sums).

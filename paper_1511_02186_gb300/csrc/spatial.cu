@@ -262,6 +262,29 @@ __global__ void tile_box_kernel(const float4 *__restrict__ nxy2, int64_t ntiles,
         boxes[t] = make_float4(x0, y0, x1, y1);
 }
 
+// One warp per group of kSuperTiles tile boxes: their union (empty tiles hold an empty box,
+// (+inf, +inf, -inf, -inf), which the union ignores).
+__global__ void super_box_kernel(const float4 *__restrict__ tbox, int64_t ntiles,
+                                 int64_t nsuper, float4 *boxes)
+{
+    const int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nsuper)
+        return;
+    const int64_t t = s * kSuperTiles + lane;
+    float4 b = make_float4(CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+    if (lane < kSuperTiles && t < ntiles)
+        b = tbox[t];
+    for (int o = 16; o > 0; o >>= 1) {
+        b.x = fminf(b.x, __shfl_xor_sync(0xffffffffu, b.x, o));
+        b.y = fminf(b.y, __shfl_xor_sync(0xffffffffu, b.y, o));
+        b.z = fmaxf(b.z, __shfl_xor_sync(0xffffffffu, b.z, o));
+        b.w = fmaxf(b.w, __shfl_xor_sync(0xffffffffu, b.w, o));
+    }
+    if (lane == 0)
+        boxes[s] = b;
+}
+
 // Morton keys of FP64 query coordinates (rounded to FP32 for the key: the key only orders).
 __global__ void morton_keys_f64_kernel(const double *__restrict__ x,
                                        const double *__restrict__ y, int64_t n,
@@ -366,6 +389,15 @@ cudaError_t tile_boxes(const float4 *nxy2, int64_t ntiles, float4 *boxes, cudaSt
 {
     tile_box_kernel<kTileF32Knn>
         <<<grid_for(ntiles * 32, 256, 1 << 20), 256, 0, st>>>(nxy2, ntiles, boxes);
+    return cudaGetLastError();
+}
+
+cudaError_t super_tile_boxes(const float4 *tile_boxes, int64_t ntiles, int64_t nsuper,
+                             float4 *boxes, cudaStream_t st)
+{
+    static_assert(kSuperTiles == 32, "one lane per tile of a super-tile");
+    super_box_kernel<<<grid_for(nsuper * 32, 256, 1 << 20), 256, 0, st>>>(tile_boxes, ntiles,
+                                                                          nsuper, boxes);
     return cudaGetLastError();
 }
 

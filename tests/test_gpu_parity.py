@@ -360,11 +360,11 @@ def test_fp64x_extreme_powers(ctx):
 
 @pytest.mark.parametrize("pattern", ["uniform", "clustered"])
 def test_fp32_pruned_knn_equals_split_scan(ctx, pattern):
-    """FP32 with enough queries for the pruned phase 1 against the forced split scan: kNN sets
-    equal up to FP32 distance ties, alpha within FP32 rounding, both Z within tolerance of the
-    oracle."""
+    """FP32 with enough queries for the pruned phase 1 (more than 32,768) against the forced
+    split scan: kNN lists equal to the oracle's up to FP32 distance ties, alpha within FP32
+    rounding, both Z within tolerance of the oracle."""
     import torch
-    wl = workloads.small_case(95, 60000, 20000, k=10, pattern=pattern, side=500.0)
+    wl = workloads.small_case(95, 30000, 60000, k=10, pattern=pattern, side=500.0)
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
     qx, qy = to_device(wl, aidw.F32C)
     p = params_of(wl, aidw.F32C)
@@ -384,6 +384,39 @@ def test_fp32_pruned_knn_equals_split_scan(ctx, pattern):
         bad = knn_mismatch(kn.cpu().numpy(), ref, src, aidw.F32C)
         assert not bad, f"kNN differs beyond ties at queries {bad[:10]}"
     assert np.abs(a1.cpu().numpy() - a2.cpu().numpy()).max() <= 1e-5
+    ds.destroy()
+
+
+@pytest.mark.parametrize("case", [(96, 60000, 20000, 10, "clustered"),
+                                  (97, 1000000 // 8, 3000, 32, "uniform"),
+                                  (98, 5000, 32768, 7, "clustered"),
+                                  (99, 4096, 100, 1, "uniform")],
+                         ids=lambda c: f"n{c[1]}m{c[2]}k{c[3]}{c[4][0]}")
+def test_fp32_warp_knn_matches_the_block_scans(ctx, case):
+    """Up to 32,768 queries the FP32 path finds each query's neighbours with one warp per query
+    (box hierarchy, bitonic merges across the lanes). Its k smallest distances are those of the
+    block scans, so alpha and Z are bit-identical to the forced split scan's with the same
+    phase-2 plan, and the lists equal the oracle's up to FP32 distance ties."""
+    import torch
+    seed, n, m, k, pat = case
+    wl = workloads.small_case(seed, n, m, k=k, pattern=pat, side=400.0)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F32C)
+    p = params_of(wl, aidw.F32C)
+    ctx.set_profiling(True)
+    z1, a1, k1 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    t1 = ctx.kernel_times()
+    assert t1.launches == 4 and t1.query_blocks == 0  # one warp per query
+    z2, a2, k2 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True,
+                                 splits=(3, t1.weight_splits))
+    assert ctx.kernel_times().splits > 1  # a split scan (at most one split per 2,048 points)
+    ctx.set_profiling(False)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2) and torch.equal(z1, z2)
+    ref, src = oracle_for(wl, aidw.F32C)
+    assert rel_err(z1.cpu().numpy(), ref).max() <= TOL_F32
+    bad = knn_mismatch(k1.cpu().numpy(), ref, src, aidw.F32C)
+    assert not bad, f"kNN differs beyond ties at queries {bad[:10]}"
     ds.destroy()
 
 

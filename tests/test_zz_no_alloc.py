@@ -55,19 +55,19 @@ def _check_against_interpolate(ctx, wl):
 
 
 def test_noalloc_matches_interpolate_twice():
-    """Two calls in a row on the pruned phase-1 route (enough queries, scratch fits), different
-    sizes, the same scratch array."""
+    """Two calls in a row on the pruned phase-1 route (more than 32,768 queries, scratch fits),
+    different sizes, the same scratch array."""
     import torch
     assert torch.cuda.is_available()
     with aidw.Context(0) as ctx:
-        for wl in (workloads.small_case(201, 40000, 30000, k=10, pattern="clustered"),
+        for wl in (workloads.small_case(201, 40000, 60000, k=10, pattern="clustered"),
                    workloads.small_case(202, 25000, 50000, k=15, pattern="uniform")):
             _check_against_interpolate(ctx, wl)
 
 
-def test_noalloc_split_scan_routes():
-    """Few queries (split scan, as aidw_interpolate) and more queries than the pruned route's
-    scratch allows at k = 10 (split scan with fewer splits)."""
+def test_noalloc_other_routes():
+    """Fewer queries (one warp per query, as aidw_interpolate) and more queries than the pruned
+    route's scratch allows at k = 10 (split scan with fewer splits)."""
     with aidw.Context(0) as ctx:
         for wl in (workloads.small_case(204, 30000, 3000, k=10, pattern="clustered"),
                    workloads.small_case(205, 6000, 230000, k=10, pattern="uniform")):
