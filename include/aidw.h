@@ -174,10 +174,10 @@ int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const float *qx, co
  * (blocks of 256 data points staged in shared memory for the thread block, Sec. 3.1.1), and the
  * data in layout AIDW_LAYOUT_SOA (x[], y[], z[]) or AIDW_LAYOUT_AOAS ({x, y, z, 0} aligned
  * structures, Sec. 3.1.3), copied from the dataset in the caller's order for the call. Precision
- * as p->precision (AIDW_F32C or AIDW_F64: float or double arrays). Per pair the FP32 arithmetic is aidw_interpolate's;
- * in FP64 the weights use the CUDA library's log2 / exp2 (aidw_interpolate's FP64 path has its
- * own table-driven pair). The four variants of one precision give identical results. Device
- * arrays only; stream-ordered.
+ * as p->precision (AIDW_F32C or AIDW_F64: float or double arrays). Per pair the FP32
+ * arithmetic is aidw_interpolate's; in FP64 the weights use the CUDA library's log2 / exp2
+ * (aidw_interpolate's FP64 path has its own table-driven pair). The four variants of one
+ * precision give identical results. Device arrays only; stream-ordered.
  * Errors: INVALID_ARG (bad version, layout, size or a host array), NOT_FOUND, OOM. */
 #define AIDW_VERSION_NAIVE 0
 #define AIDW_VERSION_TILED 1
@@ -315,9 +315,10 @@ int aidw_tune_cache_load(const char *path);
  * A large FP32 request is cut into chunks of whole 256-query blocks served by successive
  * launches, one chunk per queued request per launch, and small requests may also take an
  * express launch slot out of arrival order. An FP32 request's result does not depend on what
- * it was batched with. FP64 requests and requests with a kNN output run alone. Returns AIDW_ERR_AGAIN if the queue (4,096 requests
- * unless configured otherwise) is full: the request was not accepted, and the caller resubmits
- * later or sheds it; a request larger than the whole budget finishes with AIDW_ERR_OOM. */
+ * it was batched with. FP64 requests and requests with a kNN output run alone. Returns
+ * AIDW_ERR_AGAIN if the queue (4,096 requests unless configured otherwise) is full: the request
+ * was not accepted, and the caller resubmits later or sheds it; a request larger than the
+ * whole budget finishes with AIDW_ERR_OOM. */
 int aidw_submit(aidw_ctx *ctx, aidw_dataset ds, const void *qx, const void *qy, int64_t m,
                 const aidw_params *p, void *out, float *out_alpha, int32_t *out_knn,
                 aidw_request *out_id);
