@@ -397,7 +397,9 @@ class Context:
     def interpolate(self, ds: Dataset, qx, qy, params: Params | None = None, out=None,
                     out_alpha=None, out_knn=None, want_alpha=False, want_knn=False,
                     stream=None, splits=None):
-        """AIDW at the queries; returns (out, out_alpha or None, out_knn or None)."""
+        """AIDW at the queries; returns (out, out_alpha or None, out_knn or None).
+        `splits` (tests) forces the plan: (phase-1 splits, phase-2 splits), 0 = planned; a
+        phase-1 value of -1 forces the one-warp-per-query scan and -2 the pruned scan."""
         p = params or default_params()
         fdt = "f8" if p.precision in (F64, F64X) else "f4"
         kqx, pqx = _prep(qx, fdt)

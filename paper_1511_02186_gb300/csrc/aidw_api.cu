@@ -490,7 +490,7 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
            static_cast<double>(m) >= need;
 }
 
-// Whether an FP32 call takes the per-query phase 1 (one warp per query). Its cost grows with
+// Whether a call takes the per-query phase 1 (one warp per query). In FP32 its cost grows with
 // the query count alone (about 25 ns of the GPU per query against 1M points, 13 ns against
 // 65,536), while the block scans share their tiles among a block's queries and gain as the
 // queries get denser. Measured phase 1 (ms, against 1M uniform points / 65,536 clustered
@@ -498,14 +498,22 @@ bool use_culled_knn(int precision, const DatasetDev &ds, int64_t m, bool with_id
 //   queries        1,024   4,096   8,192   32,768   131,072
 //   block scans    2.63    3.41    4.46    1.93     1.09     /  0.61  0.64  0.73  0.54  0.46
 //   warp per query 0.24    0.25    0.34    0.99     3.24     /  0.13  0.14  0.19  0.49  1.67
-// so calls of up to kWarpKnnMaxQueries take it.
+// so FP32 calls of up to kWarpKnnMaxQueries take it. In FP64 and FP64X (exact FP64 distances
+// per lane, read through the Z-order map) the block scans cost far more, measured phase 1 (ms):
+//   queries        512    2,048  8,192  16,384  32,768  65,536  131,072  262,144
+//   1M uniform:  split scan 10.9 17.5 32.4 45.2 60.8 114 198; pruned scan 141 92.0 58.0 39.3
+//                24.3 15.4 13.1; warp per query 0.19 0.26 0.66 1.20 2.26 4.49 8.73
+//   65,536 clustered: split 3.74 5.45 10.4 13.9 20.1 39.4 77.4 145; pruned 24.9 17.5 9.24
+//                6.78 5.30 5.22 6.20 8.07; warp 0.11 0.14 0.35 0.62 1.20 2.32 4.58 9.06
+// so FP64 calls of up to kWarpKnnMaxQueriesF64 take it.
 constexpr int64_t kWarpKnnMaxQueries = 32768;
+constexpr int64_t kWarpKnnMaxQueriesF64 = 131072;
 
-bool use_warp_knn(const DatasetDev &ds, int64_t m, int sm_count)
+bool use_warp_knn(int precision, const DatasetDev &ds, int64_t m, int sm_count)
 {
     (void)ds;
     (void)sm_count;
-    return m <= kWarpKnnMaxQueries;
+    return m <= (precision == AIDW_F32C ? kWarpKnnMaxQueries : kWarpKnnMaxQueriesF64);
 }
 
 void plan_culled_knn(Plan *pl, int64_t n_pad)
@@ -597,19 +605,37 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
 // FP32 interpolation with the per-query (one warp per query) phase 1, in the caller's order:
 // phase 1, selection, phase 2, finalisation (four launches, no query ordering).
 int enqueue_warp(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
-                 const aidw_params &p, const float *qx, const float *qy, const Scratch &sc,
-                 float *out, float *out_alpha, int32_t *out_knn, cudaStream_t st, bool profile)
+                 const aidw_params &p, const void *qx, const void *qy, const Scratch &sc,
+                 void *out, float *out_alpha, int32_t *out_knn, cudaStream_t st, bool profile)
 {
     PhaseMarks marks(ctx, st, profile);
-    marks.at(0);
-    bool ok = launch_f32_knn_warp(ds, pl.m, qx, qy, p.k, sc, ctx->sm_count, st) == cudaSuccess;
-    marks.at(1);
-    ok = ok && launch_f32_select(pl, p.k, r_exp, alpha_map(p), sc, out_alpha, out_knn, st) ==
-                   cudaSuccess;
-    marks.at(2);
-    ok = ok && launch_f32_weights(ds, pl, qx, qy, sc, ctx->d_err, st) == cudaSuccess;
-    marks.at(3);
-    ok = ok && launch_f32_finalize(pl, sc, out, st) == cudaSuccess;
+    const AlphaMap am = alpha_map(p);
+    bool ok;
+    if (p.precision == AIDW_F32C) {
+        const float *fx = static_cast<const float *>(qx), *fy = static_cast<const float *>(qy);
+        marks.at(0);
+        ok = launch_f32_knn_warp(ds, pl.m, fx, fy, p.k, sc, ctx->sm_count, st) == cudaSuccess;
+        marks.at(1);
+        ok = ok && launch_f32_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st) ==
+                       cudaSuccess;
+        marks.at(2);
+        ok = ok && launch_f32_weights(ds, pl, fx, fy, sc, ctx->d_err, st) == cudaSuccess;
+        marks.at(3);
+        ok = ok && launch_f32_finalize(pl, sc, static_cast<float *>(out), st) == cudaSuccess;
+    } else {
+        const bool x = p.precision == AIDW_F64X;
+        const double *dx = static_cast<const double *>(qx), *dy = static_cast<const double *>(qy);
+        marks.at(0);
+        ok = launch_f64_knn_warp(ds, pl, dx, dy, p.k, sc, ctx->sm_count, st) == cudaSuccess;
+        marks.at(1);
+        ok = ok && launch_f64_select(pl, p.k, r_exp, am, sc, out_alpha, out_knn, st, nullptr,
+                                     x) == cudaSuccess;
+        marks.at(2);
+        ok = ok && (x ? launch_f64x_weights(ds, pl, dx, dy, sc, ctx->d_err, st)
+                      : launch_f64_weights(ds, pl, dx, dy, sc, ctx->d_err, st)) == cudaSuccess;
+        marks.at(3);
+        ok = ok && launch_f64_finalize(pl, sc, static_cast<double *>(out), st) == cudaSuccess;
+    }
     if (!ok)
         return AIDW_ERR_CUDA;
     marks.at(4);
@@ -683,14 +709,17 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         }
     }
 
-    // force_knn_splits < 0 (tests): the per-query phase 1 whatever the sizes.
-    const bool warp = p->precision == AIDW_F32C &&
-                      (force_knn_splits < 0 ||
-                       (force_knn_splits == 0 && use_warp_knn(ds, m, ctx->sm_count)));
+    // Tests force the phase-1 route: force_knn_splits -1 takes the per-query scan and -2 the
+    // pruned scan (where the dataset's tile count allows it) whatever the sizes; > 0 the split
+    // scan with that many splits.
+    const bool force_cull =
+        force_knn_splits == -2 && ds.n_pad / kTileF32Knn <= kMaxCullTiles;
+    const bool warp = force_knn_splits == -1 ||
+                      (force_knn_splits == 0 && use_warp_knn(p->precision, ds, m, ctx->sm_count));
     Plan pl = make_plan(ctx, p->precision, ds.n_pad, m, p->k, out_knn != nullptr,
                         force_knn_splits > 0 ? force_knn_splits : 0, force_w_splits, cfg);
-    const bool cull = !warp && force_knn_splits == 0 &&
-                      use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl);
+    const bool cull = force_cull || (!warp && force_knn_splits == 0 &&
+                                     use_culled_knn(p->precision, ds, m, out_knn != nullptr, pl));
     if (cull)
         plan_culled_knn(&pl, ds.n_pad);
     if (warp) {
@@ -745,9 +774,8 @@ int interpolate_impl(aidw_ctx *ctx, aidw_dataset dsid, const void *qx, const voi
         ctx_free(ctx, blk, total, st);
         return AIDW_ERR_CUDA;
     }
-    rc = warp   ? enqueue_warp(ctx, ds, r_exp, pl, *p, static_cast<const float *>(dqx),
-                               static_cast<const float *>(dqy), sc, static_cast<float *>(dout),
-                               dalpha, dknn, st, ctx->profiling)
+    rc = warp   ? enqueue_warp(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn, st,
+                               ctx->profiling)
          : cull ? enqueue_culled(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, extra, dout, dalpha, dknn,
                                  st, ctx->profiling)
                 : enqueue_interpolation(ctx, ds, r_exp, pl, *p, dqx, dqy, sc, dout, dalpha, dknn,

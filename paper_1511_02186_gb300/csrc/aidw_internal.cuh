@@ -178,6 +178,11 @@ cudaError_t launch_f64_select(const Plan &pl, int k, double r_exp, const AlphaMa
 cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const double *sqx,
                                 const double *sqy, int k, const Scratch &sc, int *err,
                                 cudaStream_t st);
+// Phase 1 with one warp per query in the caller's order (one split's lists [k][m]); with
+// pl.with_idx the lists are the k smallest (distance, caller index) pairs, as above.
+cudaError_t launch_f64_knn_warp(const DatasetDev &ds, const Plan &pl, const double *qx,
+                                const double *qy, int k, const Scratch &sc, int sm_count,
+                                cudaStream_t st);
 cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,
                                const double *qy, const Scratch &sc, int *err,
                                cudaStream_t st);

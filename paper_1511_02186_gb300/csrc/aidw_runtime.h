@@ -73,12 +73,13 @@ int enqueue_culled(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan
                    const aidw_params &p, const void *qx, const void *qy, const Scratch &sc,
                    void *extra, void *out, float *out_alpha, int32_t *out_knn, cudaStream_t st,
                    bool profile);
-// The per-query phase 1 (FP32: one warp per query, caller order): whether a call takes it, and
-// the enqueue (phase 1, selection, phase 2, finalisation; the plan keeps one list split).
-bool use_warp_knn(const DatasetDev &ds, int64_t m, int sm_count);
+// The per-query phase 1 (one warp per query, caller order): whether a call of `precision`
+// takes it, and the enqueue (phase 1, selection, phase 2, finalisation; the plan keeps one list
+// split). Query and output arrays are float for AIDW_F32C, double otherwise.
+bool use_warp_knn(int precision, const DatasetDev &ds, int64_t m, int sm_count);
 int enqueue_warp(aidw_ctx *ctx, const DatasetDev &ds, double r_exp, const Plan &pl,
-                 const aidw_params &p, const float *qx, const float *qy, const Scratch &sc,
-                 float *out, float *out_alpha, int32_t *out_knn, cudaStream_t st, bool profile);
+                 const aidw_params &p, const void *qx, const void *qy, const Scratch &sc,
+                 void *out, float *out_alpha, int32_t *out_knn, cudaStream_t st, bool profile);
 // Resolves the device address of aidw_interpolate_noalloc's scratch array on `device` (made
 // current by the caller); called once per context at aidw_init.
 int noalloc_prepare(int device);

@@ -12,6 +12,7 @@
 #include <math_constants.h>
 
 #include "aidw_internal.cuh"
+#include "warp_knn.cuh"
 
 namespace aidw {
 namespace f32dev {
@@ -356,13 +357,12 @@ static __device__ __noinline__ void fused_select_query(const float *d, int k,
 // position), scan 32 points per step with one point per lane, and take the points closer than
 // the k-th entry: a few by shifting the larger entries up one lane each, more by a bitonic sort
 // of the step's candidates and a bitonic merge with the list.
-// The points are visited through the dataset's box hierarchy (32-tile super-tiles, 512-point
-// tiles, 64-point sub-tiles), nearest box first at every level, skipping every box whose bound
-// exceeds the current k-th distance. The bounds are shrunk by 2^-20 for rounding as in
-// knn_cull_unit, so no skipped point could enter the list: the k smallest values are those of a
-// full scan. k <= 32.
+// The points are visited through the dataset's box hierarchy (warp_visit_boxes: 32-tile
+// super-tiles, 512-point tiles, 64-point sub-tiles), nearest box first at every level, skipping
+// every box whose bound exceeds the current k-th distance. The bounds are shrunk by 2^-20 for
+// rounding as in knn_cull_unit, so no skipped point could enter the list: the k smallest values
+// are those of a full scan. k <= 32.
 // ---------------------------------------------------------------------------------------------
-constexpr unsigned kFullMask = 0xffffffffu;
 // Up to this many candidates in a step are inserted one at a time; more are sorted and merged.
 constexpr int kWarpInsertMax = 6;
 
@@ -442,96 +442,48 @@ __device__ __forceinline__ void warp_scan32(const float4 *__restrict__ nxy2, int
     thr = __shfl_sync(kFullMask, ld, k - 1);
 }
 
-// Visit key of a box: its bound (the high 32 bits, so keys order by bound) and, below, the
-// distance from the query to the box centre (so that among boxes the query lies in, bound 0,
-// the one centred nearest comes first), the low 5 bits left for the lane. ~0 for an empty box.
+// Visit key of a box for an FP32 query (make_visit_key); ~0 for an empty box.
 __device__ __forceinline__ unsigned long long box_key(float qx, float qy, float4 b)
 {
-    const float lb = box_bound(qx, qy, b);
-    if (!(lb < CUDART_INF_F))
-        return ~0ull;
     const float cx = 0.5f * (b.x + b.z) - qx, cy = 0.5f * (b.y + b.w) - qy;
-    const float cd = fminf(fmaf(cx, cx, cy * cy), 3.0e38f);
-    return (static_cast<unsigned long long>(__float_as_uint(lb)) << 32) |
-           (static_cast<unsigned long long>(__float_as_uint(cd) >> 5) << 5);
+    return make_visit_key(box_bound(qx, qy, b), fmaf(cx, cx, cy * cy));
 }
 
-// The smallest of the lanes' keys with its lane in the low 5 bits; ~0 if all are ~0.
-__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long key)
-{
-    const int lane = threadIdx.x & 31;
-    if (key != ~0ull)
-        key |= static_cast<unsigned long long>(lane);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(kFullMask, key, o);
-        key = other < key ? other : key;
+// The FP32 visitor of warp_visit_boxes: the warp's list (ld, li) and its k-th entry thr.
+struct WarpKnnF32 {
+    const float4 *nxy2;
+    float qx, qy;
+    int k;
+    float ld;
+    int32_t li;
+    float thr;
+
+    __device__ __forceinline__ unsigned long long key(float4 b) const
+    {
+        return box_key(qx, qy, b);
     }
-    return key;
-}
-
-// Whether the box of a visit key may hold a point closer than thr (its bound does not exceed
-// thr); false for ~0.
-__device__ __forceinline__ bool key_open(unsigned long long key, float thr)
-{
-    return key != ~0ull && !(__uint_as_float(static_cast<uint32_t>(key >> 32)) > thr);
-}
+    // A box may hold an entering point unless its bound exceeds the k-th distance.
+    __device__ __forceinline__ bool open(unsigned long long key) const
+    {
+        return key != ~0ull && !(visit_key_bound(key) > thr);
+    }
+    __device__ __forceinline__ void scan(int64_t p)
+    {
+#pragma unroll
+        for (int u = 0; u < kSubTile; u += 32)
+            warp_scan32(nxy2, p + u, qx, qy, k, ld, li, thr);
+    }
+};
 
 // The k nearest stored points of (qx, qy) by one warp: lanes 0..k-1 end holding the k smallest
-// squared distances in ascending order (ld) and the points' stored positions (li). Boxes are
-// visited depth first, the children of each box nearest first (super-tiles in groups of 32, a
-// super-tile's 32 tiles, a tile's 8 sub-tiles; by bound, then by centre distance), each while
-// its bound does not exceed the current k-th distance: the first sub-tiles scanned are the
-// nearest, so the k-th distance falls early and the rest is mostly pruned. Empty boxes are never
-// visited.
+// squared distances in ascending order (ld) and the points' stored positions (li).
 __device__ __forceinline__ void warp_knn(const DatasetDev &ds, float qx, float qy, int k,
                                          float &ld, int32_t &li)
 {
-    constexpr int S = kTileF32Knn / kSubTile;  // 8 sub-tiles
-    const int lane = threadIdx.x & 31;
-    const int64_t ntiles = ds.n_pad / kTileF32Knn;
-    const int64_t nsuper = (ntiles + kSuperTiles - 1) / kSuperTiles;
-    ld = CUDART_INF_F;
-    li = -1;
-    float thr = CUDART_INF_F;
-    for (int64_t b = 0; b < nsuper; b += 32) {
-        const int64_t s = b + lane;
-        unsigned long long ks = s < nsuper ? box_key(qx, qy, ds.super_box[s]) : ~0ull;
-        for (;;) {
-            const unsigned long long ms = warp_min_key(ks);
-            if (!key_open(ms, thr))
-                break;
-            const int js = static_cast<int>(ms & 31ull);
-            if (lane == js)
-                ks = ~0ull;
-            const int64_t t0 = (b + js) * kSuperTiles;
-            const int64_t t = t0 + lane;
-            unsigned long long kt = t < ntiles ? box_key(qx, qy, ds.tile_box[t]) : ~0ull;
-            for (;;) {
-                const unsigned long long mt = warp_min_key(kt);
-                if (!key_open(mt, thr))
-                    break;
-                const int jt = static_cast<int>(mt & 31ull);
-                if (lane == jt)
-                    kt = ~0ull;
-                const int64_t tt = t0 + jt;
-                unsigned long long ku =
-                    lane < S ? box_key(qx, qy, ds.sub_box[tt * S + lane]) : ~0ull;
-                for (;;) {
-                    const unsigned long long mu = warp_min_key(ku);
-                    if (!key_open(mu, thr))
-                        break;
-                    const int ju = static_cast<int>(mu & 31ull);
-                    if (lane == ju)
-                        ku = ~0ull;
-                    const int64_t p = tt * kTileF32Knn + static_cast<int64_t>(ju) * kSubTile;
-#pragma unroll
-                    for (int u = 0; u < kSubTile; u += 32)
-                        warp_scan32(ds.nxy2, p + u, qx, qy, k, ld, li, thr);
-                }
-            }
-        }
-    }
+    WarpKnnF32 v{ds.nxy2, qx, qy, k, CUDART_INF_F, -1, CUDART_INF_F};
+    warp_visit_boxes(ds, v);
+    ld = v.ld;
+    li = v.li;
 }
 
 // Shared-memory scratch of a pruned phase-1 unit.

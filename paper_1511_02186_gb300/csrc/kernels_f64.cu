@@ -8,8 +8,11 @@
 // query's k-th distance, which keeps the lists exact while most pairs cost FP32 work only.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "aidw_internal.cuh"
 #include "f64_math.cuh"
+#include "warp_knn.cuh"
 
 namespace aidw {
 namespace {
@@ -464,6 +467,152 @@ f64_knn_cull_kernel(DatasetDev ds, int64_t m, int qpb, int ntiles, int ntiles_p2
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP64 phase 1 with one warp per query (the FP32 form is in f32_device.cuh): the warp's lanes
+// hold the k smallest (distance, caller index) pairs seen so far as a list sorted across the
+// lanes, 32 points are scanned per step (one per lane, read from the FP64 copy through the
+// Z-order map, exact distance as in the other FP64 scans), and the points that precede the k-th
+// entry are inserted one at a time when they are few, else sorted and merged. The pairs order by
+// distance, then caller index, so the lists are the k smallest pairs whatever the visit order:
+// those of the caller-order scan, ties going to the lower index. Boxes are walked by
+// warp_visit_boxes with FP64 bounds from the FP32 boxes widened for rounding (box_bound64).
+// ---------------------------------------------------------------------------------------------
+constexpr int kWarpInsertMax64 = 6;
+
+// (a, ai) precedes (b, bi): smaller distance, or equal distance and lower caller index.
+__device__ __forceinline__ bool pair_lt(double a, int32_t ai, double b, int32_t bi)
+{
+    return a < b || (a == b && ai < bi);
+}
+
+// Compare-exchange of a bitonic network across lanes on (distance, index) pairs.
+__device__ __forceinline__ void warp_cx64(double &v, int32_t &i, int stride, bool up)
+{
+    const double ov = __shfl_xor_sync(kFullMask, v, stride);
+    const int32_t oi = __shfl_xor_sync(kFullMask, i, stride);
+    const bool lower = (threadIdx.x & stride) == 0;
+    const bool take = (lower == up) ? pair_lt(ov, oi, v, i) : pair_lt(v, i, ov, oi);
+    if (take) {
+        v = ov;
+        i = oi;
+    }
+}
+
+// The FP64 visitor of warp_visit_boxes. Empty list entries and padding points are
+// (+inf, INT32_MAX), which no pair precedes.
+struct WarpKnnF64 {
+    const int32_t *orig;
+    const double2 *xy64;
+    double qx, qy;
+    float qxf, qyf;
+    int k;
+    double ld;     // this lane's list entry
+    int32_t li;
+    double thr;    // the k-th entry (warp-uniform)
+    int32_t thi;
+
+    __device__ __forceinline__ unsigned long long key(float4 b) const
+    {
+        if (!(b.x <= b.z))
+            return ~0ull;  // empty box
+        const float lb = __double2float_rd(box_bound64(b, qx, qy, qx, qy));
+        const float cx = 0.5f * (b.x + b.z) - qxf, cy = 0.5f * (b.y + b.w) - qyf;
+        return make_visit_key(lb, fmaf(cx, cx, cy * cy));
+    }
+    // The bound is below every distance in the box, so a box whose bound exceeds the k-th
+    // distance holds no point that precedes the k-th pair, even at a tie.
+    __device__ __forceinline__ bool open(unsigned long long key) const
+    {
+        return key != ~0ull && !(static_cast<double>(visit_key_bound(key)) > thr);
+    }
+    __device__ __forceinline__ void scan(int64_t p)
+    {
+#pragma unroll
+        for (int u = 0; u < kSubTile; u += 32)
+            scan32(p + u);
+    }
+    __device__ __forceinline__ void scan32(int64_t p)
+    {
+        const int lane = threadIdx.x & 31;
+        const int32_t o = orig[p + lane];
+        double d = CUDART_INF;
+        int32_t id = INT32_MAX;
+        if (o >= 0) {
+            const double2 pt = xy64[o];
+            d = dist2_exact(qx, qy, pt.x, pt.y);
+            id = o;
+        }
+        unsigned cand = __ballot_sync(kFullMask, pair_lt(d, id, thr, thi));
+        if (!cand)
+            return;
+        if (__popc(cand) <= kWarpInsertMax64) {
+            while (cand) {
+                const int src = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const double c = __shfl_sync(kFullMask, d, src);
+                const int32_t ci = __shfl_sync(kFullMask, id, src);
+                if (!pair_lt(c, ci, thr, thi))
+                    continue;
+                const double up = __shfl_up_sync(kFullMask, ld, 1);
+                const int32_t upi = __shfl_up_sync(kFullMask, li, 1);
+                if (pair_lt(c, ci, ld, li)) {
+                    const bool here = lane == 0 || pair_lt(up, upi, c, ci);
+                    ld = here ? c : up;
+                    li = here ? ci : upi;
+                }
+                thr = __shfl_sync(kFullMask, ld, k - 1);
+                thi = __shfl_sync(kFullMask, li, k - 1);
+            }
+            return;
+        }
+        const bool is_cand = (cand >> lane) & 1u;
+        double v = is_cand ? d : CUDART_INF;
+        int32_t vi = is_cand ? id : INT32_MAX;
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1)
+                warp_cx64(v, vi, stride, (lane & size) == 0);
+        }
+        // The 32 smallest of the two sorted lists, as a bitonic sequence, then sorted.
+        const double rv = __shfl_sync(kFullMask, v, 31 - lane);
+        const int32_t ri = __shfl_sync(kFullMask, vi, 31 - lane);
+        if (pair_lt(rv, ri, ld, li)) {
+            ld = rv;
+            li = ri;
+        }
+#pragma unroll
+        for (int stride = 16; stride > 0; stride >>= 1)
+            warp_cx64(ld, li, stride, true);
+        thr = __shfl_sync(kFullMask, ld, k - 1);
+        thi = __shfl_sync(kFullMask, li, k - 1);
+    }
+};
+
+// One warp per query (grid-stride over the queries, caller order); writes one split's lists
+// [k][m] (distances, and caller indices when part_idx is not null) for f64_select_kernel.
+__global__ void __launch_bounds__(kThreads)
+f64_knn_warp_kernel(DatasetDev ds, int64_t m, const double *__restrict__ qx,
+                    const double *__restrict__ qy, int k, double *__restrict__ part_d2,
+                    int32_t *__restrict__ part_idx)
+{
+    constexpr int W = kThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * W;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * W + (threadIdx.x >> 5); q < m;
+         q += nwarps) {
+        const double x = qx[q], y = qy[q];
+        WarpKnnF64 v{ds.orig, ds.xy64, x, y, static_cast<float>(x), static_cast<float>(y), k,
+                     CUDART_INF, INT32_MAX, CUDART_INF, INT32_MAX};
+        warp_visit_boxes(ds, v);
+        if (lane < k) {
+            part_d2[static_cast<int64_t>(lane) * m + q] = v.ld;
+            if (part_idx)
+                part_idx[static_cast<int64_t>(lane) * m + q] = v.li;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
                   const double *__restrict__ part_d2, const int32_t *__restrict__ part_idx,
@@ -788,6 +937,20 @@ cudaError_t launch_f64_knn_cull(const DatasetDev &ds, const Plan &pl, const doub
                    : launch_cull64_t<16, false>(ds, pl, sqx, sqy, k, sc, st);
     return idx ? launch_cull64_t<32, true>(ds, pl, sqx, sqy, k, sc, st)
                : launch_cull64_t<32, false>(ds, pl, sqx, sqy, k, sc, st);
+}
+
+cudaError_t launch_f64_knn_warp(const DatasetDev &ds, const Plan &pl, const double *qx,
+                                const double *qy, int k, const Scratch &sc, int sm_count,
+                                cudaStream_t st)
+{
+    constexpr int W = kThreads / 32;
+    const int64_t want = (pl.m + W - 1) / W;
+    const int64_t cap = static_cast<int64_t>(sm_count) * 16;
+    const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min(want, cap)));
+    f64_knn_warp_kernel<<<grid, kThreads, 0, st>>>(ds, pl.m, qx, qy, k,
+                                                   static_cast<double *>(sc.part_d2),
+                                                   pl.with_idx ? sc.part_idx : nullptr);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const double *qx,

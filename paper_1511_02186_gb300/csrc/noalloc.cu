@@ -93,7 +93,7 @@ extern "C" int aidw_interpolate_noalloc(aidw_ctx *ctx, aidw_dataset ds, const fl
     const Plan planned = make_plan(ctx, AIDW_F32C, dev.n_pad, m, p->k, false, 0, 0);
 
     // Per-query phase 1 where aidw_interpolate would take it (one list per query, no ordering).
-    if (use_warp_knn(dev, m, 0)) {
+    if (use_warp_knn(AIDW_F32C, dev, m, 0)) {
         Plan pl = planned;
         pl.knn.splits = 1;
         pl.knn.split_len = dev.n_pad;

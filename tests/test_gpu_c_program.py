@@ -144,7 +144,7 @@ def test_c_program_interpolates_on_the_gpu(tmp_path):
                         os.path.join(ROOT, "include"), str(src), lib_path,
                         f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    # One warp per query in FP32 phase 1 (20,000 queries), the pruned FP64 phase 1, clustered data.
+    # One warp per query in FP32 and FP64 phase 1 (20,000 queries), clustered data.
     wl = workloads.small_case(301, 30000, 20000, k=10, pattern="clustered")
     for name in ("x", "y", "z", "qx", "qy"):
         np.ascontiguousarray(getattr(wl, name), dtype=np.float64).tofile(tmp_path / name)

@@ -295,30 +295,70 @@ def _fp64_cases():
 @pytest.mark.parametrize("idx", range(5), ids=["uniform", "clustered_k17", "clustered_k32",
                                                "lattice_ties", "large_offset"])
 def test_fp64_pruned_knn_equals_caller_order_scan(ctx, idx):
-    """FP64 with enough queries takes the pruned phase 1 over Z-ordered queries, with or without
-    the kNN output (then the lists hold the k smallest (distance, caller index) pairs); forced
-    splits take the caller-order scan. All give bit-identical alpha and Z and the oracle's kNN
-    lists bit for bit (ties to the lower index), and Z within 1e-12 of the oracle."""
+    """The three FP64 phase-1 scans: the pruned scan over Z-ordered queries, the caller-order
+    split scan and one warp per query, each with and without the kNN output (then the lists hold
+    the k smallest (distance, caller index) pairs). All give bit-identical alpha and Z and the
+    oracle's kNN lists bit for bit (ties to the lower index), and Z within 1e-12 of the oracle;
+    the planned route gives the same."""
     import torch
     wl = _fp64_cases()[idx]
     ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
     qx, qy = to_device(wl, aidw.F64)
     p = aidw.default_params(k=wl.k, precision=aidw.F64)
     ctx.set_profiling(True)
-    z1, a1, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True)
+    z1, a1, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True, splits=(-2, 0))
     assert ctx.kernel_times().launches == 18  # ordering + pruned phase 1
-    z2, a2, kn2 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
+    z2, a2, kn2 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True, splits=(-2, 0))
     assert ctx.kernel_times().launches == 18
     z3, a3, kn3 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True, splits=(4, 0))
-    assert ctx.kernel_times().launches == 4   # caller-order scan
+    t3 = ctx.kernel_times()
+    assert t3.launches == 4 and t3.query_blocks > 0  # caller-order scan
+    z4, a4, kn4 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True,
+                                  splits=(-1, 0))
+    t4 = ctx.kernel_times()
+    assert t4.launches == 4 and t4.query_blocks == 0  # one warp per query
+    z5, a5, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True, splits=(-1, 0))
+    z0, a0, kn0 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True)
     ctx.set_profiling(False)
     torch.cuda.synchronize()
-    assert torch.equal(a1, a2) and torch.equal(a1, a3)
-    assert torch.equal(z1, z2) and torch.equal(z1, z3)
+    for a, z in ((a2, z2), (a3, z3), (a4, z4), (a5, z5), (a0, z0)):
+        assert torch.equal(a1, a) and torch.equal(z1, z)
     ref, src = oracle_for(wl, aidw.F64)
     assert rel_err(z1.cpu().numpy(), ref).max() <= TOL_F64
-    assert np.array_equal(kn2.cpu().numpy(), ref["knn"])
-    assert np.array_equal(kn3.cpu().numpy(), ref["knn"])
+    for kn in (kn2, kn3, kn4, kn0):
+        assert np.array_equal(kn.cpu().numpy(), ref["knn"])
+    ds.destroy()
+
+
+@pytest.mark.parametrize("case", [(111, 1_000_000, 300, 10, "uniform"),
+                                  (112, 60000, 2000, 32, "clustered"),
+                                  (113, 4096, 777, 1, "uniform"),
+                                  (114, 2049, 5000, 7, "clustered")],
+                         ids=["1M_300q", "clustered_k32", "k1", "ragged_2049"])
+def test_fp64_warp_knn_few_queries(ctx, case):
+    """FP64 and FP64X calls with few queries against datasets from 2,049 points (padding tiles
+    with empty boxes) to 1M, k from 1 to 32: the one-warp-per-query phase 1 gives the oracle's
+    kNN lists bit for bit, alpha within 2e-6 of the maximum level and Z within 1e-12; alpha
+    and Z equal the caller-order scan's bit for bit."""
+    import torch
+    seed, n, m, k, pat = case
+    wl = workloads.small_case(seed, n, m, k=k, pattern=pat, side=600.0)
+    ds = ctx.create_dataset(wl.x, wl.y, wl.z, wl.area)
+    qx, qy = to_device(wl, aidw.F64)
+    ref, src = oracle_for(wl, aidw.F64)
+    for prec in (aidw.F64, aidw.F64X):
+        p = params_of(wl, prec)
+        ctx.set_profiling(True)
+        z1, a1, k1 = ctx.interpolate(ds, qx, qy, p, want_alpha=True, want_knn=True,
+                                     splits=(-1, 0))
+        assert ctx.kernel_times().query_blocks == 0
+        z2, a2, _ = ctx.interpolate(ds, qx, qy, p, want_alpha=True, splits=(3, 0))
+        ctx.set_profiling(False)
+        torch.cuda.synchronize()
+        assert torch.equal(a1, a2) and torch.equal(z1, z2)
+        assert np.array_equal(k1.cpu().numpy(), ref["knn"])
+        assert np.abs(a1.cpu().numpy() - ref["alpha"]).max() <= 2e-6 * 5.0
+        assert rel_err(z1.cpu().numpy(), ref).max() <= TOL_F64
     ds.destroy()
 
 
