@@ -3,12 +3,12 @@
 both beside this script. Run ``python gen_f64_math_tables.py``.
 
 Method (after Tang's table-driven logarithm and exponential):
-  log2(x): x = 2^e m, m in [1, 2); F = 1 + j/1024 from the top 10 bits of m; r = (m - F) / F
-           in [0, 2^-10); log2(x) = e + log2(F) + log2(1 + r) with the degree-5 Taylor
-           polynomial of ln(1 + r) divided by ln 2 (truncation below 2^-62).
-  exp2(y): k = round(256 y), r = y - k/256 in [-1/512, 1/512]; 2^y = 2^(k >> 8)
-           * 2^((k & 255)/256) * e^(r ln 2) with a degree-4 Taylor polynomial (truncation below
-           2^-54 relative).
+  log2(x): x = 2^e m, m in [1, 2); F = 1 + j/2048 from the top 11 bits of m; r = (m - F) / F
+           in [0, 2^-11); log2(x) = e + log2(F) + log2(1 + r) with the degree-4 Taylor
+           polynomial of ln(1 + r) divided by ln 2 (truncation below 2^-56.8).
+  exp2(y): k = round(2048 y), r = y - k/2048 in [-2^-12, 2^-12]; 2^y = 2^(k >> 11)
+           * 2^((k & 2047)/2048) * e^(r ln 2) with a degree-3 Taylor polynomial (truncation
+           below 2^-54.7 relative).
 Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bits):
   log2(x): F = 1 + j/256 from the top 8 bits of the mantissa; u = (m - F) / (F ln 2) by the
            pair (1 / (F ln 2)); log2(1 + r) = u - (ln 2 / 2) u^2 + sum_{i=3..6} c_i u^i with
@@ -39,8 +39,8 @@ def lit(x) -> str:
     return float.hex(dbl(x))
 
 
-def table(name, values, per_line=3):
-    out = [f"__device__ __constant__ double {name}[{len(values)}] = {{"]
+def table(name, values, per_line=3, space="__device__ __constant__"):
+    out = [f"{space} double {name}[{len(values)}] = {{"]
     for i in range(0, len(values), per_line):
         out.append("    " + ", ".join(lit(v) for v in values[i:i + per_line]) + ",")
     out.append("};")
@@ -103,20 +103,21 @@ def df_tables(ln2):
 
 def main():
     ln2 = mp.log(2)
-    log2_f = [mp.log(1 + mp.mpf(j) / 1024) / ln2 for j in range(1024)]
-    inv_f = [1 / (1 + mp.mpf(j) / 1024) for j in range(1024)]
-    exp2_j = [mp.power(2, mp.mpf(j) / 256) for j in range(256)]
-    ln_coef = [mp.mpf((-1) ** (i + 1)) / i / ln2 for i in range(1, 6)]    # r, r^2 .. r^5
-    exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 5)]          # 1, r ln2 .. r^4
+    log2_f = [mp.log(1 + mp.mpf(j) / 2048) / ln2 for j in range(2048)]
+    inv_f = [1 / (1 + mp.mpf(j) / 2048) for j in range(2048)]
+    exp2_j = [mp.power(2, mp.mpf(j) / 2048) for j in range(2048)]
+    ln_coef = [mp.mpf((-1) ** (i + 1)) / i / ln2 for i in range(1, 5)]    # r, r^2 .. r^4
+    exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 4)]          # 1, r ln2 .. r^3
+    dev = "__device__ const"  # 48 KB: global memory, copied to shared memory per CTA
     lines = [
         "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
         "// (values rounded to the nearest double, written as exact hexadecimal literals).",
-        table("kLog2F", log2_f),
-        table("kInvF", inv_f),
-        table("kExp2J", exp2_j),
-        "// log2(1 + r) = sum_{i=1..5} kL2C<i> r^i",
+        table("kLog2F", log2_f, space=dev),
+        table("kInvF", inv_f, space=dev),
+        table("kExp2J", exp2_j, space=dev),
+        "// log2(1 + r) = sum_{i=1..4} kL2C<i> r^i",
         *(f"constexpr double kL2C{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
-        "// e^(r ln 2) = sum_{i=0..4} kExpC<i> r^i",
+        "// e^(r ln 2) = sum_{i=0..3} kExpC<i> r^i",
         *(f"constexpr double kExpC{i} = {lit(c)};" for i, c in enumerate(exp_coef)),
         "",
     ]

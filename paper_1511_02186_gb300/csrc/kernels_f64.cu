@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kChunkKnn = 16;
 constexpr int kChunkW = 32;
-constexpr int kQW64 = 2;
+constexpr int kQW64 = 4;
 
 __device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
 {
@@ -681,8 +681,10 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     qp[q] = o;
 }
 
+// Three CTAs per SM (24 KB of tiles plus 48 KB of tables each); the minimum-blocks bound also
+// keeps the compiler from a 64-register allocation that spills.
 template <int Q>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
                    const double *__restrict__ qy, const QParamF64 *__restrict__ qp,
                    double *__restrict__ part_sum, int *__restrict__ err)
@@ -690,7 +692,8 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
     __shared__ __align__(128) double2 txy[2][kTileF64W];
     __shared__ __align__(128) double tz[2][kTileF64W];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ f64math::Tables tabs;
+    extern __shared__ double2 f64_dyn[];  // f64math::Tables (kTablesBytes)
+    f64math::Tables &tabs = *reinterpret_cast<f64math::Tables *>(f64_dyn);
 
     const int tid = threadIdx.x;
     const int s = blockIdx.y;
@@ -869,10 +872,23 @@ int f64_knn_slots_per_sm(int k, bool with_idx)
     return knn_slots_t<32>(with_idx);
 }
 
+// The FP64 phase-2 kernel takes its log2 / exp2 tables in dynamic shared memory.
+cudaError_t prepare_f64_weights()
+{
+    return cudaFuncSetAttribute(f64_weights_kernel<kQW64>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(f64math::kTablesBytes));
+}
+
 int f64_w_slots_per_sm()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_weights_kernel<kQW64>, kThreads, 0);
+    if (prepare_f64_weights() != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_weights_kernel<kQW64>, kThreads,
+                                                  f64math::kTablesBytes);
     return n > 0 ? n : 1;
 }
 
@@ -957,7 +973,10 @@ cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const doubl
                                const double *qy, const Scratch &sc, int *err, cudaStream_t st)
 {
     dim3 grid(pl.w.qblocks, pl.w.splits);
-    f64_weights_kernel<kQW64><<<grid, kThreads, 0, st>>>(
+    const cudaError_t e = prepare_f64_weights();
+    if (e != cudaSuccess)
+        return e;
+    f64_weights_kernel<kQW64><<<grid, kThreads, f64math::kTablesBytes, st>>>(
         ds, pl.m, pl.w, qx, qy, static_cast<const QParamF64 *>(sc.qparam),
         static_cast<double *>(sc.part_sum), err);
     return cudaGetLastError();
@@ -981,7 +1000,8 @@ __global__ void f64_math_probe_kernel(const double *__restrict__ x, const double
                                       int64_t n, double *__restrict__ lx,
                                       double *__restrict__ ey)
 {
-    __shared__ f64math::Tables tabs;
+    extern __shared__ double2 f64_dyn[];  // f64math::Tables (kTablesBytes)
+    f64math::Tables &tabs = *reinterpret_cast<f64math::Tables *>(f64_dyn);
     f64math::load_tables(tabs);
     __syncthreads();
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
@@ -1001,6 +1021,10 @@ extern "C" int aidw_debug_f64_log2_exp2(const double *x, const double *y, int64_
     if (n == 0)
         return AIDW_OK;
     const unsigned blocks = static_cast<unsigned>(n < 256 * 1024 ? (n + 255) / 256 : 1024);
-    aidw::f64_math_probe_kernel<<<blocks, 256>>>(x, y, n, lx, ey);
+    if (cudaFuncSetAttribute(aidw::f64_math_probe_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(aidw::f64math::kTablesBytes)) != cudaSuccess)
+        return AIDW_ERR_CUDA;
+    aidw::f64_math_probe_kernel<<<blocks, 256, aidw::f64math::kTablesBytes>>>(x, y, n, lx, ey);
     return cudaDeviceSynchronize() == cudaSuccess ? AIDW_OK : AIDW_ERR_CUDA;
 }

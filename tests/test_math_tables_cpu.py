@@ -20,8 +20,8 @@ def parse(path):
     """name -> list of values (arrays) or value (scalars) of a table file."""
     text = open(path).read()
     out = {}
-    for m in re.finditer(r"__constant__ (?:double|float) (\w+)\[(\d+)\] = \{(.*?)\};", text,
-                         re.S):
+    for m in re.finditer(r"__device__ (?:__constant__|const) (?:double|float) (\w+)\[(\d+)\] = "
+                         r"\{(.*?)\};", text, re.S):
         vals = [float.fromhex(t.strip().rstrip("f")) for t in m.group(3).split(",") if t.strip()]
         assert len(vals) == int(m.group(2)), m.group(1)
         out[m.group(1)] = vals
@@ -61,21 +61,21 @@ def prec():
 def test_fp64_tables_are_nearest_doubles(prec):
     t = parse(os.path.join(CSRC, "f64_math_tables.inc"))
     ln2 = mp.log(2)
-    assert len(t["kLog2F"]) == 1024 and len(t["kInvF"]) == 1024 and len(t["kExp2J"]) == 256
-    for j in range(1024):
-        f = 1 + mp.mpf(j) / 1024
+    assert len(t["kLog2F"]) == 2048 and len(t["kInvF"]) == 2048 and len(t["kExp2J"]) == 2048
+    for j in range(2048):
+        f = 1 + mp.mpf(j) / 2048
         assert nearest_double(t["kLog2F"][j], mp.log(f) / ln2), j
         assert nearest_double(t["kInvF"][j], 1 / f), j
-    for j in range(256):
-        assert nearest_double(t["kExp2J"][j], mp.power(2, mp.mpf(j) / 256)), j
+        assert nearest_double(t["kExp2J"][j], mp.power(2, mp.mpf(j) / 2048)), j
     # log2(1 + r) = sum (-1)^(i+1) r^i / (i ln 2); e^(r ln 2) = sum (r ln 2)^i / i!
-    for i in range(1, 6):
+    for i in range(1, 5):
         assert nearest_double(t[f"kL2C{i}"], mp.mpf((-1) ** (i + 1)) / (i * ln2)), i
-    for i in range(0, 5):
+    assert "kL2C5" not in t and "kExpC4" not in t
+    for i in range(0, 4):
         assert nearest_double(t[f"kExpC{i}"], ln2 ** i / mp.factorial(i)), i
     # The exact anchors the coincidence rule and powers of two rely on.
     assert t["kLog2F"][0] == 0.0 and t["kInvF"][0] == 1.0 and t["kExp2J"][0] == 1.0
-    assert t["kInvF"][512] == float.fromhex("0x1.5555555555555p-1")  # 1 / 1.5, rounded
+    assert t["kInvF"][1024] == float.fromhex("0x1.5555555555555p-1")  # 1 / 1.5, rounded
 
 
 def test_double_float_tables_are_accurate_pairs(prec):
