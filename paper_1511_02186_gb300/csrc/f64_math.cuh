@@ -9,12 +9,14 @@
 //     error about one ulp of max(1, |log2 x|).
 //   exp2(y), y < 1023: y <= -1021 gives 0 (far below any weight that matters next to the nearest
 //     point's, which is 1); else k = round(2048 y), r = y - k/2048 in [-2^-12, 2^-12] (exact),
-//     2^y = 2^(k >> 11) * 2^((k & 2047)/2048) * e^(r ln 2) with a degree-3 Taylor polynomial;
-//     the power of two is added to the exponent field. Relative error a few ulps.
+//     2^y = 2^(k >> 11) * T_j e^(r ln 2), T_j = 2^(j/2048), j = k & 2047, with the degree-3
+//     Taylor polynomial multiplied out with T_j (its four coefficients tabulated per j, so three
+//     fused steps evaluate it); the power of two is added to the exponent field. Relative error
+//     a few ulps.
 // GB300 runs FP64 arithmetic at 2 operations per clock per SM against 64 integer operations, so
 // every step whose result is exact is done on the integer pipe from the operands' bits: the
 // range tests, m - F, e as a double, and exp2's reduction (k and r). The FP64 pipe runs only the
-// rounded operations: 6 for log2 and 4 for exp2, against several times that for the general
+// rounded operations: 6 for log2 and 3 for exp2, against several times that for the general
 // library functions; the weights of Eq. 1 need the absolute accuracy of log2 (it is scaled by
 // alpha / 2 and exponentiated), which these keep.
 #pragma once
@@ -36,10 +38,11 @@ constexpr int kExpBits = 11;                   // exp2 table: 2^(j / 2048)
 constexpr int kExpN = 1 << kExpBits;
 constexpr long long kMant = 0x000FFFFFFFFFFFFFLL;
 
-// Shared-memory copy of the tables for one CTA (48 KB: dynamic shared memory).
+// Shared-memory copy of the tables for one CTA (96 KB: dynamic shared memory).
 struct Tables {
     double2 lf[kLogN];  // (log2 F_j, 1 / F_j)
-    double e2[kExpN];   // 2^(j/2048)
+    double2 ea[kExpN];  // (T_j, T_j ln 2)
+    double2 eb[kExpN];  // (T_j (ln 2)^2 / 2, T_j (ln 2)^3 / 6)
 };
 constexpr size_t kTablesBytes = sizeof(Tables);
 
@@ -48,8 +51,10 @@ __device__ __forceinline__ void load_tables(Tables &t)
 {
     for (int i = threadIdx.x; i < kLogN; i += blockDim.x)
         t.lf[i] = make_double2(kLog2F[i], kInvF[i]);
-    for (int i = threadIdx.x; i < kExpN; i += blockDim.x)
-        t.e2[i] = kExp2J[i];
+    for (int i = threadIdx.x; i < kExpN; i += blockDim.x) {
+        t.ea[i] = make_double2(kExp2J[i], kExp2C1[i]);
+        t.eb[i] = make_double2(kExp2C2[i], kExp2C3[i]);
+    }
 }
 
 __device__ __forceinline__ int log2_index(double x)
@@ -135,11 +140,10 @@ __device__ __forceinline__ double exp2_t(double y, const Tables &t)
         r = flip_sign(scaled_int(static_cast<unsigned long long>(rm < 0 ? -rm : rm), E), neg_r);
         k = b < 0 ? -static_cast<long long>(ka) : static_cast<long long>(ka);
     }
-    // T e^(r ln 2) = T (1 + r q(r)).
-    double q = __fma_rn(kExpC3, r, kExpC2);
-    q = __fma_rn(q, r, kExpC1);
-    const double T = t.e2[static_cast<int>(k & (kExpN - 1))];
-    const double v = __fma_rn(T, __dmul_rn(r, q), T);
+    // T_j e^(r ln 2) = ((c3 r + c2) r + c1) r + T_j.
+    const int j = static_cast<int>(k & (kExpN - 1));
+    const double2 a = t.ea[j], c = t.eb[j];
+    const double v = __fma_rn(r, __fma_rn(r, __fma_rn(r, c.y, c.x), a.y), a.x);
     return __longlong_as_double(__double_as_longlong(v) + ((k >> kExpBits) << 52));
 }
 

@@ -7,8 +7,10 @@ Method (after Tang's table-driven logarithm and exponential):
            in [0, 2^-11); log2(x) = e + log2(F) + log2(1 + r) with the degree-4 Taylor
            polynomial of ln(1 + r) divided by ln 2 (truncation below 2^-56.8).
   exp2(y): k = round(2048 y), r = y - k/2048 in [-2^-12, 2^-12]; 2^y = 2^(k >> 11)
-           * 2^((k & 2047)/2048) * e^(r ln 2) with a degree-3 Taylor polynomial (truncation
-           below 2^-54.7 relative).
+           * T_j e^(r ln 2), T_j = 2^(j/2048), j = k & 2047, with the degree-3 Taylor polynomial
+           of e^(r ln 2) multiplied out with T_j: T_j + T_j ln 2 r + T_j (ln 2)^2/2 r^2
+           + T_j (ln 2)^3/6 r^3, each coefficient tabulated per j (truncation below 2^-54.7
+           relative).
 Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bits):
   log2(x): F = 1 + j/256 from the top 8 bits of the mantissa; u = (m - F) / (F ln 2) by the
            pair (1 / (F ln 2)); log2(1 + r) = u - (ln 2 / 2) u^2 + sum_{i=3..6} c_i u^i with
@@ -106,19 +108,19 @@ def main():
     log2_f = [mp.log(1 + mp.mpf(j) / 2048) / ln2 for j in range(2048)]
     inv_f = [1 / (1 + mp.mpf(j) / 2048) for j in range(2048)]
     exp2_j = [mp.power(2, mp.mpf(j) / 2048) for j in range(2048)]
+    exp2_c = [[t * ln2 ** i / mp.factorial(i) for t in exp2_j] for i in range(1, 4)]
     ln_coef = [mp.mpf((-1) ** (i + 1)) / i / ln2 for i in range(1, 5)]    # r, r^2 .. r^4
-    exp_coef = [ln2 ** i / mp.factorial(i) for i in range(0, 4)]          # 1, r ln2 .. r^3
-    dev = "__device__ const"  # 48 KB: global memory, copied to shared memory per CTA
+    dev = "__device__ const"  # 96 KB: global memory, copied to shared memory per CTA
     lines = [
         "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
         "// (values rounded to the nearest double, written as exact hexadecimal literals).",
         table("kLog2F", log2_f, space=dev),
         table("kInvF", inv_f, space=dev),
         table("kExp2J", exp2_j, space=dev),
+        "// T_j (ln 2)^i / i!, i = 1, 2, 3: the exp2 polynomial's coefficients for entry j",
+        *(table(f"kExp2C{i + 1}", c, space=dev) for i, c in enumerate(exp2_c)),
         "// log2(1 + r) = sum_{i=1..4} kL2C<i> r^i",
         *(f"constexpr double kL2C{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
-        "// e^(r ln 2) = sum_{i=0..3} kExpC<i> r^i",
-        *(f"constexpr double kExpC{i} = {lit(c)};" for i, c in enumerate(exp_coef)),
         "",
     ]
     path = os.path.join(HERE, "f64_math_tables.inc")

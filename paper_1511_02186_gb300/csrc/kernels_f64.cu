@@ -20,6 +20,7 @@ namespace {
 constexpr int kChunkKnn = 16;
 constexpr int kChunkW = 32;
 constexpr int kQW64 = 4;
+constexpr int kTileW64 = 256;  // FP64 phase-2 tile (points), beside 96 KB of tables
 
 __device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
 {
@@ -681,16 +682,16 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     qp[q] = o;
 }
 
-// Three CTAs per SM (24 KB of tiles plus 48 KB of tables each); the minimum-blocks bound also
-// keeps the compiler from a 64-register allocation that spills.
+// Two CTAs per SM (12 KB of 256-point tiles plus 96 KB of tables each); the minimum-blocks
+// bound also keeps the compiler from a 64-register allocation that spills.
 template <int Q>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
 f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
                    const double *__restrict__ qy, const QParamF64 *__restrict__ qp,
                    double *__restrict__ part_sum, int *__restrict__ err)
 {
-    __shared__ __align__(128) double2 txy[2][kTileF64W];
-    __shared__ __align__(128) double tz[2][kTileF64W];
+    __shared__ __align__(128) double2 txy[2][kTileW64];
+    __shared__ __align__(128) double tz[2][kTileW64];
     __shared__ __align__(8) uint64_t bar[2];
     extern __shared__ double2 f64_dyn[];  // f64math::Tables (kTablesBytes)
     f64math::Tables &tabs = *reinterpret_cast<f64math::Tables *>(f64_dyn);
@@ -701,7 +702,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
     const int64_t qbase = static_cast<int64_t>(blockIdx.x) * pp.q_per_block;
     const int64_t p_begin = static_cast<int64_t>(s) * pp.split_len;
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
-    const int ntiles = static_cast<int>((p_end - p_begin) / kTileF64W);
+    const int ntiles = static_cast<int>((p_end - p_begin) / kTileW64);
 
     double qxr[Q], qyr[Q], ns[Q], cc[Q], hw[Q], cw[Q], hz[Q], cz[Q];
 #pragma unroll
@@ -720,11 +721,11 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
         fence_mbar_init();
     }
     __syncthreads();
-    constexpr uint32_t kBxy = kTileF64W * sizeof(double2);
-    constexpr uint32_t kBz = kTileF64W * sizeof(double);
+    constexpr uint32_t kBxy = kTileW64 * sizeof(double2);
+    constexpr uint32_t kBz = kTileW64 * sizeof(double);
     if (tid == 0) {
         for (int t = 0; t < 2 && t < ntiles; ++t) {
-            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileF64W;
+            const int64_t o = p_begin + static_cast<int64_t>(t) * kTileW64;
             mbar_arrive_expect_tx(&bar[t], kBxy + kBz);
             tma_load_1d(txy[t], ds.xy64 + o, kBxy, &bar[t]);
             tma_load_1d(tz[t], ds.z64 + o, kBz, &bar[t]);
@@ -742,7 +743,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
             }
             break;
         }
-        for (int c = 0; c < kTileF64W; c += kChunkW) {
+        for (int c = 0; c < kTileW64; c += kChunkW) {
             double sw[Q], sz[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j)
@@ -769,7 +770,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) {
             fence_proxy_async_smem();
-            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileF64W;
+            const int64_t o = p_begin + static_cast<int64_t>(t + 2) * kTileW64;
             mbar_arrive_expect_tx(&bar[b], kBxy + kBz);
             tma_load_1d(txy[b], ds.xy64 + o, kBxy, &bar[b]);
             tma_load_1d(tz[b], ds.z64 + o, kBz, &bar[b]);
