@@ -3,14 +3,15 @@
 both beside this script. Run ``python gen_f64_math_tables.py``.
 
 Method (after Tang's table-driven logarithm and exponential):
-  log2(x): x = 2^e m, m in [1, 2); F = 1 + j/2048 from the top 11 bits of m; r = (m - F) / F
-           in [0, 2^-11); log2(x) = e + log2(F) + log2(1 + r) with the degree-4 Taylor
-           polynomial of ln(1 + r) divided by ln 2 (truncation below 2^-56.8).
-  exp2(y): k = round(2048 y), r = y - k/2048 in [-2^-12, 2^-12]; 2^y = 2^(k >> 11)
-           * T_j e^(r ln 2), T_j = 2^(j/2048), j = k & 2047, with the degree-3 Taylor polynomial
-           of e^(r ln 2) multiplied out with T_j: T_j + T_j ln 2 r + T_j (ln 2)^2/2 r^2
-           + T_j (ln 2)^3/6 r^3, each coefficient tabulated per j (truncation below 2^-54.7
-           relative).
+  log2(x): x = 2^e (F + u), F = 1 + j/1024 from the top 10 bits of the mantissa, u in
+           [0, 2^-10) the rest (exact); log2(x) = e + log2(F) + u q_j(u) with a cubic q_j per
+           entry, the polynomial interpolating log2(1 + u/F) / u at the Chebyshev nodes of
+           [0, 2^-10] (near-minimax; the error of u q_j(u) is below 2^-58.5, less than the
+           rounding of log2 F_j).
+  exp2(y): k = round(1024 y), r = y - k/1024 in [-2^-11, 2^-11]; 2^y = 2^(k >> 10)
+           * T_j 2^r, T_j = 2^(j/1024), j = k & 1023, with T_j 2^r = T_j + r q_j(r) and q_j the
+           quadratic interpolating T_j (2^r - 1) / r at the Chebyshev nodes of [-2^-11, 2^-11]
+           (relative error below 2^-52.5, about half an ulp of T_j).
 Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bits):
   log2(x): F = 1 + j/256 from the top 8 bits of the mantissa; u = (m - F) / (F ln 2) by the
            pair (1 / (F ln 2)); log2(1 + r) = u - (ln 2 / 2) u^2 + sum_{i=3..6} c_i u^i with
@@ -103,24 +104,51 @@ def df_tables(ln2):
     return "\n".join(lines)
 
 
+def cheb_fit(g, a, b, deg):
+    """Coefficients c_0..c_deg of the polynomial interpolating g at the deg + 1 Chebyshev nodes
+    of [a, b] (near the minimax polynomial of that degree), at the working precision."""
+    n = deg + 1
+    xs = [(a + b) / 2 - (b - a) / 2 * mp.cos((2 * i + 1) * mp.pi / (2 * n)) for i in range(n)]
+    A = mp.matrix([[x ** k for k in range(n)] for x in xs])
+    c = mp.lu_solve(A, mp.matrix([g(x) for x in xs]))
+    return [c[k] for k in range(n)]
+
+
 def main():
     ln2 = mp.log(2)
-    log2_f = [mp.log(1 + mp.mpf(j) / 2048) / ln2 for j in range(2048)]
-    inv_f = [1 / (1 + mp.mpf(j) / 2048) for j in range(2048)]
-    exp2_j = [mp.power(2, mp.mpf(j) / 2048) for j in range(2048)]
-    exp2_c = [[t * ln2 ** i / mp.factorial(i) for t in exp2_j] for i in range(1, 4)]
-    ln_coef = [mp.mpf((-1) ** (i + 1)) / i / ln2 for i in range(1, 5)]    # r, r^2 .. r^4
-    dev = "__device__ const"  # 96 KB: global memory, copied to shared memory per CTA
+    dev = "__device__ const"  # 72 KB: global memory, copied to shared memory per CTA
+    # log2: x = 2^e (F_j + u), F_j = 1 + j/1024, u in [0, 2^-10) exact; log2(1 + u/F_j) = u q_j(u)
+    # with q_j the cubic through g(u) = log2(1 + u/F_j) / u (g(0) = 1 / (F_j ln 2)) at the
+    # Chebyshev nodes of [0, 2^-10].
+    h = mp.mpf(2) ** -10
+    log2_f, l2d = [], [[], [], [], []]
+    for j in range(1024):
+        F = 1 + mp.mpf(j) / 1024
+        log2_f.append(mp.log(F) / ln2)
+        c = cheb_fit(lambda u: mp.log1p(u / F) / (u * ln2), 0, h, 3)
+        for i in range(4):
+            l2d[i].append(c[i])
+    # exp2: y = k/1024 + r, r in [-2^-11, 2^-11]; T_j 2^r = T_j + r q_j(r), T_j = 2^(j/1024),
+    # q_j the quadratic through T_j (2^r - 1) / r (T_j ln 2 at 0) at the Chebyshev nodes.
+    he = mp.mpf(2) ** -11
+    exp2_j, e2e = [], [[], [], []]
+    for j in range(1024):
+        T = mp.power(2, mp.mpf(j) / 1024)
+        exp2_j.append(T)
+        c = cheb_fit(lambda r: T * ln2 if r == 0 else T * mp.expm1(r * ln2) / r, -he, he, 2)
+        for i in range(3):
+            e2e[i].append(c[i])
     lines = [
         "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
         "// (values rounded to the nearest double, written as exact hexadecimal literals).",
+        "// log2 F_j, F_j = 1 + j/1024",
         table("kLog2F", log2_f, space=dev),
-        table("kInvF", inv_f, space=dev),
+        "// log2(1 + u/F_j) = u (kL2D1 + kL2D2 u + kL2D3 u^2 + kL2D4 u^3)[j], u in [0, 2^-10)",
+        *(table(f"kL2D{i + 1}", l2d[i], space=dev) for i in range(4)),
+        "// T_j = 2^(j/1024)",
         table("kExp2J", exp2_j, space=dev),
-        "// T_j (ln 2)^i / i!, i = 1, 2, 3: the exp2 polynomial's coefficients for entry j",
-        *(table(f"kExp2C{i + 1}", c, space=dev) for i, c in enumerate(exp2_c)),
-        "// log2(1 + r) = sum_{i=1..4} kL2C<i> r^i",
-        *(f"constexpr double kL2C{i + 1} = {lit(c)};" for i, c in enumerate(ln_coef)),
+        "// T_j 2^r = T_j + r (kExp2E1 + kExp2E2 r + kExp2E3 r^2)[j], r in [-2^-11, 2^-11]",
+        *(table(f"kExp2E{i + 1}", e2e[i], space=dev) for i in range(3)),
         "",
     ]
     path = os.path.join(HERE, "f64_math_tables.inc")

@@ -20,7 +20,7 @@ namespace {
 constexpr int kChunkKnn = 16;
 constexpr int kChunkW = 32;
 constexpr int kQW64 = 4;
-constexpr int kTileW64 = 256;  // FP64 phase-2 tile (points), beside 96 KB of tables
+constexpr int kTileW64 = 256;  // FP64 phase-2 tile (points), beside 72 KB of tables
 
 __device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
 {
@@ -682,7 +682,7 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     qp[q] = o;
 }
 
-// Two CTAs per SM (12 KB of 256-point tiles plus 96 KB of tables each); the minimum-blocks
+// Two CTAs per SM (12 KB of 256-point tiles plus 72 KB of tables each); the minimum-blocks
 // bound also keeps the compiler from a 64-register allocation that spills.
 template <int Q>
 __global__ void __launch_bounds__(kThreads, 2)

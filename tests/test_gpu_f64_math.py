@@ -80,24 +80,24 @@ def test_special_values():
 
 def test_integer_reduction_edges():
     """The steps done on the integer pipe at their edges. exp2: arguments at and around the
-    rounding points of k = round(2048 y) (k/2048 +- half a step, +- an ulp), arguments so small
-    that k = 0 (|2048 y| < 1/4), negative and positive; log2: mantissas whose bits below the
-    11-bit table index are all ones or a single one, and the neighbours of powers of two. All
+    rounding points of k = round(1024 y) (k/1024 +- half a step, +- an ulp), arguments so small
+    that k = 0 (|1024 y| < 1/4), negative and positive; log2: mantissas whose bits below the
+    10-bit table index are all ones or a single one, and the neighbours of powers of two. All
     within the same bounds as above."""
     rng = np.random.default_rng(5)
-    k = rng.integers(-2 * 1020 * 1024, 8 * 2048, 4096).astype(np.float64)
-    step = 1.0 / 2048
+    k = rng.integers(-1020 * 1024, 8 * 1024, 4096).astype(np.float64)
+    step = 1.0 / 1024
     y = np.concatenate([k * step, (k + 0.5) * step, (k - 0.5) * step,
                         np.nextafter((k + 0.5) * step, np.inf),
                         np.nextafter((k + 0.5) * step, -np.inf),
-                        rng.uniform(-2.0 ** -14, 2.0 ** -14, 2048),
-                        2.0 ** rng.uniform(-60, -12, 2048) * rng.choice([-1.0, 1.0], 2048)])
+                        rng.uniform(-2.0 ** -13, 2.0 ** -13, 2048),
+                        2.0 ** rng.uniform(-60, -11, 2048) * rng.choice([-1.0, 1.0], 2048)])
     y = y[(y > -1020.99) & (y < 8.0)]
     e = rng.integers(-1000, 1000, 2048).astype(np.float64)
     p2 = 2.0 ** e
-    mant = rng.integers(0, 2048, 2048)
-    ones = (1.0 + mant / 2048.0 + (2.0 ** -11 - 2.0 ** -52)) * p2   # low 41 bits all ones
-    one = (1.0 + mant / 2048.0 + 2.0 ** -52) * p2                   # a single low bit
+    mant = rng.integers(0, 1024, 2048)
+    ones = (1.0 + mant / 1024.0 + (2.0 ** -10 - 2.0 ** -52)) * p2   # low 42 bits all ones
+    one = (1.0 + mant / 1024.0 + 2.0 ** -52) * p2                   # a single low bit
     x = np.concatenate([ones, one, np.nextafter(p2, np.inf), np.nextafter(p2, 0.0)])
     n = max(len(x), len(y))
     xs = np.resize(x, n)
@@ -109,6 +109,6 @@ def test_integer_reduction_edges():
     ref_e = np.exp2(ys)
     err_e = np.abs(ey / ref_e - 1.0)
     assert err_e.max() <= 4 * ULP1 / 2, err_e.max()
-    # k/2048 itself: exact up to the table entry's rounding (r = 0).
+    # k/1024 itself: exact up to the table entry's rounding (r = 0).
     lk, ek = probe(np.ones(16), np.arange(-8, 8) * step)
     assert np.all(np.abs(ek / np.exp2(np.arange(-8, 8) * step) - 1.0) <= ULP1)

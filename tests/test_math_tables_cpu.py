@@ -58,26 +58,37 @@ def prec():
     mp.mp.prec = old
 
 
-def test_fp64_tables_are_nearest_doubles(prec):
+def test_fp64_tables_are_accurate(prec):
+    """log2 F_j and T_j are the nearest doubles to their values; each entry's polynomial, with
+    its coefficients as stored, is within its stated bound of the function at 9 points of its
+    interval (evaluated exactly in 120-bit arithmetic): |log2 F_j + u q_j(u) - log2(F_j + u)|
+    below 2^-53.5 for u in [0, 2^-10] (the rounding of log2 F_j dominates), |T_j + r q_j(r) -
+    T_j 2^r| below 2^-51.5 T_j for r in [-2^-11, 2^-11] (half an ulp of T_j and the cubic's
+    error, about an ulp)."""
     t = parse(os.path.join(CSRC, "f64_math_tables.inc"))
     ln2 = mp.log(2)
-    assert len(t["kLog2F"]) == 2048 and len(t["kInvF"]) == 2048 and len(t["kExp2J"]) == 2048
-    for j in range(2048):
-        f = 1 + mp.mpf(j) / 2048
-        assert nearest_double(t["kLog2F"][j], mp.log(f) / ln2), j
-        assert nearest_double(t["kInvF"][j], 1 / f), j
-        T = mp.power(2, mp.mpf(j) / 2048)
+    for name in ("kLog2F", "kL2D1", "kL2D2", "kL2D3", "kL2D4", "kExp2J", "kExp2E1", "kExp2E2",
+                 "kExp2E3"):
+        assert len(t[name]) == 1024, name
+    h, he = mp.mpf(2) ** -10, mp.mpf(2) ** -11
+    us = [h * i / 8 for i in range(9)]
+    rs = [he * (i - 4) / 4 for i in range(9)]
+    for j in range(1024):
+        F = 1 + mp.mpf(j) / 1024
+        assert nearest_double(t["kLog2F"][j], mp.log(F) / ln2), j
+        d = [mp.mpf(t[f"kL2D{i}"][j]) for i in range(1, 5)]
+        for u in us:
+            p = mp.mpf(t["kLog2F"][j]) + u * (d[0] + u * (d[1] + u * (d[2] + u * d[3])))
+            assert abs(p - mp.log(F + u) / ln2) < mp.mpf(2) ** -53.5, (j, u)
+        T = mp.power(2, mp.mpf(j) / 1024)
         assert nearest_double(t["kExp2J"][j], T), j
-        # e^(r ln 2) = sum (r ln 2)^i / i!, multiplied out with T_j
-        for i in range(1, 4):
-            assert nearest_double(t[f"kExp2C{i}"][j], T * ln2 ** i / mp.factorial(i)), (i, j)
-    # log2(1 + r) = sum (-1)^(i+1) r^i / (i ln 2)
-    for i in range(1, 5):
-        assert nearest_double(t[f"kL2C{i}"], mp.mpf((-1) ** (i + 1)) / (i * ln2)), i
-    assert "kL2C5" not in t
+        e = [mp.mpf(t[f"kExp2E{i}"][j]) for i in range(1, 4)]
+        for r in rs:
+            p = mp.mpf(t["kExp2J"][j]) + r * (e[0] + r * (e[1] + r * e[2]))
+            assert abs(p - T * mp.power(2, r)) < T * mp.mpf(2) ** -51.5, (j, r)
     # The exact anchors the coincidence rule and powers of two rely on.
-    assert t["kLog2F"][0] == 0.0 and t["kInvF"][0] == 1.0 and t["kExp2J"][0] == 1.0
-    assert t["kInvF"][1024] == float.fromhex("0x1.5555555555555p-1")  # 1 / 1.5, rounded
+    assert t["kLog2F"][0] == 0.0 and t["kExp2J"][0] == 1.0
+    assert t["kExp2J"][512] == float.fromhex("0x1.6a09e667f3bcdp+0")  # sqrt(2), rounded
 
 
 def test_double_float_tables_are_accurate_pairs(prec):
