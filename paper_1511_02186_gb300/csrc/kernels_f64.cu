@@ -682,6 +682,31 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     qp[q] = o;
 }
 
+// Sum of the weights of one query as an unsigned fixed-point integer with 96 fractional bits,
+// accumulated exactly on the integer pipe (weights are at most 1 + a few ulps, the nearest
+// point's being 1, so the sum of any n < 2^31 of them fits; each weight is truncated below
+// 2^-96, at most n 2^-96 in all against a sum of at least 1): one FP64 addition per pair fewer.
+__device__ __forceinline__ unsigned __int128 weight_fixed(double w)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
+    const int E = static_cast<int>(b >> 52);  // w >= 0
+    const unsigned long long M =
+        (b & 0x000FFFFFFFFFFFFFull) | (E != 0 ? (1ull << 52) : 0ull);
+    const int sh = E - (1075 - 96);  // w 2^96 = M 2^sh
+    const unsigned __int128 m128 = M;
+    return sh >= 0 ? (m128 << sh) : (m128 >> (-sh < 127 ? -sh : 127));
+}
+
+// The fixed-point sum as two doubles whose sum is within 2^-100 of it, relative.
+__device__ __forceinline__ void fixed_to_doubles(unsigned __int128 v, double &hi, double &lo)
+{
+    const unsigned long long A = static_cast<unsigned long long>(v >> 64);
+    const unsigned long long B = static_cast<unsigned long long>(v);
+    hi = __ull2double_rn(A) * 0x1p-32;
+    const long long dA = static_cast<long long>(A - __double2ull_rn(hi * 0x1p32));  // exact
+    lo = __ll2double_rn(dA) * 0x1p-32 + __ull2double_rn(B) * 0x1p-96;
+}
+
 // Two CTAs per SM (12 KB of 256-point tiles plus 72 KB of tables each); the minimum-blocks
 // bound also keeps the compiler from a 64-register allocation that spills.
 template <int Q>
@@ -704,7 +729,8 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
     const int64_t p_end = min(p_begin + pp.split_len, ds.n_pad);
     const int ntiles = static_cast<int>((p_end - p_begin) / kTileW64);
 
-    double qxr[Q], qyr[Q], ns[Q], cc[Q], hw[Q], cw[Q], hz[Q], cz[Q];
+    double qxr[Q], qyr[Q], ns[Q], cc[Q], hz[Q], cz[Q];
+    unsigned __int128 aw[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int64_t q = min(qbase + j * kThreads + tid, m - 1);
@@ -713,7 +739,8 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
         const QParamF64 o = qp[q];
         ns[j] = o.neg_s;
         cc[j] = o.c;
-        hw[j] = cw[j] = hz[j] = cz[j] = 0.0;
+        hz[j] = cz[j] = 0.0;
+        aw[j] = 0;
     }
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -744,10 +771,10 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
             break;
         }
         for (int c = 0; c < kTileW64; c += kChunkW) {
-            double sw[Q], sz[Q];
+            double sz[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j)
-                sw[j] = sz[j] = 0.0;
+                sz[j] = 0.0;
 #pragma unroll 4
             for (int u = 0; u < kChunkW; ++u) {
                 const double2 p = txy[b][c + u];
@@ -757,15 +784,13 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
                     const double d2 = dist2_eps(qxr[j], qyr[j], p.x, p.y);
                     const double w = f64math::exp2_t(
                         __fma_rn(f64math::log2_t(d2, tabs), ns[j], cc[j]), tabs);
-                    sw[j] = __dadd_rn(sw[j], w);
+                    aw[j] += weight_fixed(w);
                     sz[j] = __fma_rn(w, pz, sz[j]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                kahan_add(hw[j], cw[j], sw[j]);
+            for (int j = 0; j < Q; ++j)
                 kahan_add(hz[j], cz[j], sz[j]);
-            }
         }
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) {
@@ -784,8 +809,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
         if (q >= m)
             continue;
         double *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
-        o[0] = hw[j];
-        o[m] = -cw[j];
+        fixed_to_doubles(aw[j], o[0], o[m]);
         o[2 * m] = hz[j];
         o[3 * m] = -cz[j];
     }
