@@ -743,9 +743,8 @@ def run_gpu(args):
     fp64_rate = q64 * wl.n / (e0.elapsed_time(e1) / 1e3)
     # FP64 phase 2 against the FP64 pipe: FP64 instructions per pair of the kernel as written
     # (distance 4, table log2 5, power scale 1, table exp2 3, the weighted sum 1; the sum of the
-    # weights is exact on the integer pipe, and so are the exact steps of log2
-    # and exp2 run on the integer pipe) at 2 per clock per SM,
-    # GB300's nominal FP64 rate (1.25 TFLOP/s) and the pipe's peak that ncu reports.
+    # weights and the exact steps of log2 and exp2 run on the integer pipe) at 2 per clock per
+    # SM, GB300's nominal FP64 rate (1.25 TFLOP/s) and the pipe's peak that ncu reports.
     fp64_w_achieved = q64 * wl.n / (kt64.weights_ms / 1e3)
     fp64_w_peak = sm * clk_hz * FP64_PIPE_PER_CLK_SM / FP64_OPS_P2
 
