@@ -694,7 +694,8 @@ __device__ __forceinline__ unsigned __int128 weight_fixed(double w)
         (b & 0x000FFFFFFFFFFFFFull) | (E != 0 ? (1ull << 52) : 0ull);
     const int sh = E - (1075 - 96);  // w 2^96 = M 2^sh
     const unsigned __int128 m128 = M;
-    return sh >= 0 ? (m128 << sh) : (m128 >> (-sh < 127 ? -sh : 127));
+    // (Shifts are kept below 128: a weight is never +inf or NaN here, but no shift is undefined.)
+    return sh >= 0 ? (m128 << (sh < 127 ? sh : 127)) : (m128 >> (-sh < 127 ? -sh : 127));
 }
 
 // The fixed-point sum as two doubles whose sum is within 2^-100 of it, relative.
