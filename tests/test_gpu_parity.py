@@ -491,17 +491,52 @@ def _degenerate_cases():
     out.append(workloads.Workload("offset_1e5", x, y, np.cos(x / 7), 2500.0,
                                   1.0e5 + rng.uniform(0, 50, 3000),
                                   2.0e5 + rng.uniform(0, 50, 3000), k=10))
+    # Queries far outside the data's box (every data point far and at nearly the same
+    # distance: R large, alpha at the top level, the weights nearly equal).
+    x, y = rng.uniform(0, 1, 6000), rng.uniform(0, 1, 6000)
+    out.append(workloads.Workload("far_queries", x, y, np.sin(7 * x) * y, 1.0,
+                                  rng.uniform(300, 301, 2000), rng.uniform(-301, -300, 2000),
+                                  k=10))
     return out
 
 
+# Phase-1 routes a test can force (one warp per query, the pruned scan over Z-ordered queries,
+# the split scan with three data splits), each with the same phase-2 plan (two data splits).
+ROUTES = {"warp": (-1, 2), "pruned": (-2, 2), "split3": (3, 2)}
+
+
+DEGENERATE_IDS = ["one_location", "k_equals_n", "collinear", "two_clusters", "offset_1e5",
+                  "far_queries"]
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("idx", range(5), ids=["one_location", "k_equals_n", "collinear",
-                                               "two_clusters", "offset_1e5"])
+@pytest.mark.parametrize("idx", range(len(DEGENERATE_IDS)), ids=DEGENERATE_IDS)
 def test_degenerate_inputs(ctx, precision, idx):
-    """Zero-area and zero-width data, k = n, weights spanning hundreds of decades, and large
-    coordinate offsets: the same parity as the regular cases."""
+    """Zero-area and zero-width data, k = n, weights spanning hundreds of decades, large
+    coordinate offsets and queries far outside the data: the same parity as the regular
+    cases."""
     wl = _degenerate_cases()[idx]
     assert_parity(ctx, wl, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("idx", range(len(DEGENERATE_IDS)), ids=DEGENERATE_IDS)
+def test_degenerate_inputs_every_phase1_route(ctx, precision, idx):
+    """The degenerate geometries through each phase-1 scan, whatever the sizes would pick: one
+    warp per query, the pruned scan (its tile and sub-tile boxes of zero width or area, a query
+    block's box far from every tile) and the split scan. Each route meets the oracle's bar (Z,
+    alpha, kNN lists up to FP32 ties; FP64 lists bit for bit), and alpha and Z agree between
+    the routes bit for bit (they keep the same k smallest distances)."""
+    wl = _degenerate_cases()[idx]
+    runs = {}
+    for name, splits in ROUTES.items():
+        runs[name] = run_gpu(ctx, wl, precision, want_knn=True, splits=splits)
+        assert_parity(ctx, wl, precision, gpu=runs[name])
+    z0, a0, _ = runs["warp"]
+    for name in ("pruned", "split3"):
+        z, a, _ = runs[name]
+        assert np.array_equal(a, a0), f"{wl.name}: alpha differs between warp and {name}"
+        assert np.array_equal(z, z0), f"{wl.name}: Z differs between warp and {name}"
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
