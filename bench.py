@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 # bounding-box bounds), so it has no per-pair minimum; a step's n * m pair-evaluations are bound
 # by phase 2.
 FP32_OPS_P2, MUFU_OPS_P2 = 7, 2
-FP64_OPS_P2 = 14  # FP64 instructions per pair in the FP64 phase-2 kernel
+FP64_OPS_P2 = 6  # FP64 instructions per pair in the FP64 phase-2 kernel
 FP64X_OPS_P2 = 4  # FP64 instructions per pair in the AIDW_F64X phase-2 kernel (the distance)
 FP64_PIPE_PER_CLK_SM = 2.0  # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 DFMA per clk per SM
 LANES_PER_SM = 128  # FP32 lanes and issue slots (4 schedulers x 32) per SM per clock
@@ -742,9 +742,9 @@ def run_gpu(args):
     ctx.set_profiling(False)
     fp64_rate = q64 * wl.n / (e0.elapsed_time(e1) / 1e3)
     # FP64 phase 2 against the FP64 pipe: FP64 instructions per pair of the kernel as written
-    # (distance 4, table log2 5, power scale 1, table exp2 3, the weighted sum 1; the sum of the
-    # weights and the exact steps of log2 and exp2 run on the integer pipe) at 2 per clock per
-    # SM, GB300's nominal FP64 rate (1.25 TFLOP/s) and the pipe's peak that ncu reports.
+    # (distance 4, power scale 1, the weighted sum 1; log2, exp2 and the sum of the weights run
+    # in fixed point on the integer pipe) at 2 per clock per SM, GB300's nominal FP64 rate
+    # (1.25 TFLOP/s) and the pipe's peak that ncu reports.
     fp64_w_achieved = q64 * wl.n / (kt64.weights_ms / 1e3)
     fp64_w_peak = sm * clk_hz * FP64_PIPE_PER_CLK_SM / FP64_OPS_P2
 

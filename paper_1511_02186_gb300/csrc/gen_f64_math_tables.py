@@ -1,4 +1,4 @@
-"""Writes the constant tables of the table-driven log2 / exp2 of the phase-2 scans: the FP64 ones
+"""Writes the constant tables of the table-driven log2 / exp2 of the phase-2 scans: the FP64 path's
 (``f64_math_tables.inc``) and the double-float ones of the AIDW_F64X scan (``df_math_tables.inc``),
 both beside this script. Run ``python gen_f64_math_tables.py``.
 
@@ -6,12 +6,15 @@ Method (after Tang's table-driven logarithm and exponential):
   log2(x): x = 2^e (F + u), F = 1 + j/1024 from the top 10 bits of the mantissa, u in
            [0, 2^-10) the rest (exact); log2(x) = e + log2(F) + u q_j(u) with a cubic q_j per
            entry, the polynomial interpolating log2(1 + u/F) / u at the Chebyshev nodes of
-           [0, 2^-10] (near-minimax; the error of u q_j(u) is below 2^-58.5, less than the
-           rounding of log2 F_j).
+           [0, 2^-10] (near-minimax; the error of u q_j(u) is below 2^-58.5).
   exp2(y): k = round(1024 y), r = y - k/1024 in [-2^-11, 2^-11]; 2^y = 2^(k >> 10)
            * T_j 2^r, T_j = 2^(j/1024), j = k & 1023, with T_j 2^r = T_j + r q_j(r) and q_j the
            quadratic interpolating T_j (2^r - 1) / r at the Chebyshev nodes of [-2^-11, 2^-11]
-           (relative error below 2^-52.5, about half an ulp of T_j).
+           (relative error at most 2^-52.7).
+The FP64 path evaluates both in unsigned fixed point on the integer pipe, so its tables hold
+every value as the nearest integer to value * 2^62 (all values are below 2), q_j's coefficients
+of log2 as magnitudes (their signs alternate, the same for every entry: +, -, +, -), those of
+exp2 as they are (all positive).
 Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bits):
   log2(x): F = 1 + j/256 from the top 8 bits of the mantissa; u = (m - F) / (F ln 2) by the
            pair (1 / (F ln 2)); log2(1 + r) = u - (ln 2 / 2) u^2 + sum_{i=3..6} c_i u^i with
@@ -19,9 +22,10 @@ Double-float (a value as the unevaluated sum hi + lo of two floats, about 48 bit
   exp2(y): k = round(128 y), s = y - k/128, t = s ln 2 in [-2^-8.5, 2^-8.5]; 2^y = 2^(k >> 7)
            * 2^((k & 127)/128) * e^t with e^t - 1 = t + t^2/2 + t^3 (1/6 + t/24 + t^2/120)
            (the t^6 term is below 2^-61).
-Every value is evaluated with 200-bit arithmetic and rounded to the nearest double (FP64
-tables) or split into the nearest float and the nearest float to the remainder (double-float
-tables); the files hold them as hexadecimal floating-point literals (exact).
+Every value is evaluated with 200-bit arithmetic and rounded to the nearest integer multiple of
+2^-62 (FP64 path's tables, written as hexadecimal integer literals) or split into the nearest
+float and the nearest float to the remainder (double-float tables, written as exact hexadecimal
+floating-point literals).
 """
 import os
 
@@ -38,14 +42,22 @@ def dbl(x) -> float:
     return libmp.to_float(mp.mpf(x)._mpf_, rnd=libmp.round_nearest)
 
 
-def lit(x) -> str:
-    return float.hex(dbl(x))
+FX_BITS = 62  # fixed-point tables: value * 2^62
 
 
-def table(name, values, per_line=3, space="__device__ __constant__"):
-    out = [f"{space} double {name}[{len(values)}] = {{"]
+def fx(x) -> int:
+    """Nearest integer to the mpf x * 2^62."""
+    return int(mp.nint(mp.mpf(x) * mp.mpf(2) ** FX_BITS))
+
+
+def ilit(v: int) -> str:
+    return ("-" if v < 0 else "") + f"0x{abs(v):016x}LL"
+
+
+def fx_table(name, values, per_line=3, space="__device__ const"):
+    out = [f"{space} long long {name}[{len(values)}] = {{"]
     for i in range(0, len(values), per_line):
-        out.append("    " + ", ".join(lit(v) for v in values[i:i + per_line]) + ",")
+        out.append("    " + ", ".join(ilit(fx(v)) for v in values[i:i + per_line]) + ",")
     out.append("};")
     return "\n".join(out)
 
@@ -139,16 +151,19 @@ def main():
         for i in range(3):
             e2e[i].append(c[i])
     lines = [
-        "// Generated by gen_f64_math_tables.py: constants of the table-driven FP64 log2 / exp2",
-        "// (values rounded to the nearest double, written as exact hexadecimal literals).",
+        "// Generated by gen_f64_math_tables.py: constants of the FP64 path's table-driven log2 /",
+        "// exp2, in fixed point: every entry the nearest integer to value * 2^62.",
         "// log2 F_j, F_j = 1 + j/1024",
-        table("kLog2F", log2_f, space=dev),
-        "// log2(1 + u/F_j) = u (kL2D1 + kL2D2 u + kL2D3 u^2 + kL2D4 u^3)[j], u in [0, 2^-10)",
-        *(table(f"kL2D{i + 1}", l2d[i], space=dev) for i in range(4)),
+        fx_table("kFxLog2F", log2_f, space=dev),
+        "// log2(1 + u/F_j) = u (kFxL2A1 - kFxL2A2 u + kFxL2A3 u^2 - kFxL2A4 u^3)[j] 2^-62,",
+        "// u in [0, 2^-10)",
+        *(fx_table(f"kFxL2A{i + 1}", [(-1) ** i * c for c in l2d[i]], space=dev)
+          for i in range(4)),
         "// T_j = 2^(j/1024)",
-        table("kExp2J", exp2_j, space=dev),
-        "// T_j 2^r = T_j + r (kExp2E1 + kExp2E2 r + kExp2E3 r^2)[j], r in [-2^-11, 2^-11]",
-        *(table(f"kExp2E{i + 1}", e2e[i], space=dev) for i in range(3)),
+        fx_table("kFxExp2T", exp2_j, space=dev),
+        "// T_j 2^r = (kFxExp2T + r (kFxExp2E1 + kFxExp2E2 r + kFxExp2E3 r^2))[j] 2^-62,",
+        "// r in [-2^-11, 2^-11]",
+        *(fx_table(f"kFxExp2E{i + 1}", e2e[i], space=dev) for i in range(3)),
         "",
     ]
     path = os.path.join(HERE, "f64_math_tables.inc")

@@ -21,6 +21,9 @@ constexpr int kChunkKnn = 16;
 constexpr int kChunkW = 32;
 constexpr int kQW64 = 4;
 constexpr int kTileW64 = 256;  // FP64 phase-2 tile (points), beside 72 KB of tables
+// FP64 phase-2 CTA: 8 warps share one copy of the tables (two CTAs per SM by shared memory, 16
+// warps: the integer steps of log2 / exp2 are long dependent chains that need the warps).
+constexpr int kThreadsW64 = 256;
 
 __device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
 {
@@ -682,21 +685,11 @@ f64_select_kernel(int64_t m, int S, int k, double r_exp, AlphaMap am,
     qp[q] = o;
 }
 
-// Sum of the weights of one query as an unsigned fixed-point integer with 96 fractional bits,
-// accumulated exactly on the integer pipe (weights are at most 1 + a few ulps, the nearest
-// point's being 1, so the sum of any n < 2^31 of them fits; each weight is truncated below
-// 2^-96, at most n 2^-96 in all against a sum of at least 1): one FP64 addition per pair fewer.
-__device__ __forceinline__ unsigned __int128 weight_fixed(double w)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
-    const int E = static_cast<int>(b >> 52);  // w >= 0
-    const unsigned long long M =
-        (b & 0x000FFFFFFFFFFFFFull) | (E != 0 ? (1ull << 52) : 0ull);
-    const int sh = E - (1075 - 96);  // w 2^96 = M 2^sh
-    const unsigned __int128 m128 = M;
-    // (Shifts are kept below 128: a weight is never +inf or NaN here, but no shift is undefined.)
-    return sh >= 0 ? (m128 << (sh < 127 ? sh : 127)) : (m128 >> (-sh < 127 ? -sh : 127));
-}
+// The sum of the weights of one query is kept as an unsigned fixed-point integer with 96
+// fraction bits, accumulated exactly on the integer pipe from the weights exp2_t gives in that
+// form (weights are at most 1 + a few ulps, the nearest point's being 1, so the sum of any
+// n < 2^31 of them fits; each weight is truncated below 2^-96, at most n 2^-96 in all against a
+// sum of at least 1).
 
 // The fixed-point sum as two doubles whose sum is within 2^-100 of it, relative.
 __device__ __forceinline__ void fixed_to_doubles(unsigned __int128 v, double &hi, double &lo)
@@ -708,10 +701,10 @@ __device__ __forceinline__ void fixed_to_doubles(unsigned __int128 v, double &hi
     lo = __ll2double_rn(dA) * 0x1p-32 + __ull2double_rn(B) * 0x1p-96;
 }
 
-// Two CTAs per SM (12 KB of 256-point tiles plus 72 KB of tables each); the minimum-blocks
-// bound also keeps the compiler from a 64-register allocation that spills.
+// Two CTAs of 256 threads per SM (12 KB of 256-point tiles plus 72 KB of tables each, 128
+// registers a thread).
 template <int Q>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreadsW64, 2)
 f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
                    const double *__restrict__ qy, const QParamF64 *__restrict__ qp,
                    double *__restrict__ part_sum, int *__restrict__ err)
@@ -734,7 +727,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
     unsigned __int128 aw[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const int64_t q = min(qbase + j * kThreads + tid, m - 1);
+        const int64_t q = min(qbase + j * kThreadsW64 + tid, m - 1);
         qxr[j] = qx[q];
         qyr[j] = qy[q];
         const QParamF64 o = qp[q];
@@ -783,9 +776,10 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
                     const double d2 = dist2_eps(qxr[j], qyr[j], p.x, p.y);
-                    const double w = f64math::exp2_t(
-                        __fma_rn(f64math::log2_t(d2, tabs), ns[j], cc[j]), tabs);
-                    aw[j] += weight_fixed(w);
+                    unsigned __int128 w96;
+                    const double w = f64math::exp2_t<true>(
+                        __fma_rn(f64math::log2_t(d2, tabs), ns[j], cc[j]), tabs, &w96);
+                    aw[j] += w96;
                     sz[j] = __fma_rn(w, pz, sz[j]);
                 }
             }
@@ -806,7 +800,7 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
         return;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const int64_t q = qbase + j * kThreads + tid;
+        const int64_t q = qbase + j * kThreadsW64 + tid;
         if (q >= m)
             continue;
         double *o = part_sum + static_cast<int64_t>(s) * 4 * m + q;
@@ -886,7 +880,7 @@ int f64_knn_queries_per_block(int k)
 
 int f64_w_queries_per_block()
 {
-    return kThreads * kQW64;
+    return kThreadsW64 * kQW64;
 }
 
 int f64_knn_slots_per_sm(int k, bool with_idx)
@@ -913,7 +907,7 @@ int f64_w_slots_per_sm()
         cudaGetLastError();
         return 1;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_weights_kernel<kQW64>, kThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f64_weights_kernel<kQW64>, kThreadsW64,
                                                   f64math::kTablesBytes);
     return n > 0 ? n : 1;
 }
@@ -1002,7 +996,7 @@ cudaError_t launch_f64_weights(const DatasetDev &ds, const Plan &pl, const doubl
     const cudaError_t e = prepare_f64_weights();
     if (e != cudaSuccess)
         return e;
-    f64_weights_kernel<kQW64><<<grid, kThreads, f64math::kTablesBytes, st>>>(
+    f64_weights_kernel<kQW64><<<grid, kThreadsW64, f64math::kTablesBytes, st>>>(
         ds, pl.m, pl.w, qx, qy, static_cast<const QParamF64 *>(sc.qparam),
         static_cast<double *>(sc.part_sum), err);
     return cudaGetLastError();
@@ -1033,7 +1027,7 @@ __global__ void f64_math_probe_kernel(const double *__restrict__ x, const double
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         lx[i] = f64math::log2_t(x[i], tabs);
-        ey[i] = f64math::exp2_t(y[i], tabs);
+        ey[i] = f64math::exp2_t<false>(y[i], tabs, nullptr);
     }
 }
 }  // namespace

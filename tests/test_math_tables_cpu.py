@@ -1,8 +1,8 @@
 """The constant tables of the phase-2 log2 / exp2, checked on the CPU against their definitions
-with 120-bit arithmetic: csrc/f64_math_tables.inc (the FP64 scan: every entry the nearest double
-to its value) and csrc/df_math_tables.inc (the FP64X scan: every pair hi + lo within 2^-48 of
-its value, relative, with hi the nearest float and |lo| at most half an ulp of hi). The files
-are also what the generator script writes, bit for bit."""
+with 120-bit arithmetic: csrc/f64_math_tables.inc (the FP64 scan, in fixed point: every entry
+the nearest integer to its value * 2^62) and csrc/df_math_tables.inc (the FP64X scan: every pair
+hi + lo within 2^-48 of its value, relative, with hi the nearest float and |lo| at most half an
+ulp of hi). The files are also what the generator script writes, bit for bit."""
 import importlib.util
 import os
 import re
@@ -23,6 +23,10 @@ def parse(path):
     for m in re.finditer(r"__device__ (?:__constant__|const) (?:double|float) (\w+)\[(\d+)\] = "
                          r"\{(.*?)\};", text, re.S):
         vals = [float.fromhex(t.strip().rstrip("f")) for t in m.group(3).split(",") if t.strip()]
+        assert len(vals) == int(m.group(2)), m.group(1)
+        out[m.group(1)] = vals
+    for m in re.finditer(r"__device__ const long long (\w+)\[(\d+)\] = \{(.*?)\};", text, re.S):
+        vals = [int(t.strip().rstrip("L"), 16) for t in m.group(3).split(",") if t.strip()]
         assert len(vals) == int(m.group(2)), m.group(1)
         out[m.group(1)] = vals
     for m in re.finditer(r"constexpr (?:double|float) (\w+) = ([^;]+);", text):
@@ -59,36 +63,38 @@ def prec():
 
 
 def test_fp64_tables_are_accurate(prec):
-    """log2 F_j and T_j are the nearest doubles to their values; each entry's polynomial, with
-    its coefficients as stored, is within its stated bound of the function at 9 points of its
-    interval (evaluated exactly in 120-bit arithmetic): |log2 F_j + u q_j(u) - log2(F_j + u)|
-    below 2^-53.5 for u in [0, 2^-10] (the rounding of log2 F_j dominates), |T_j + r q_j(r) -
-    T_j 2^r| below 2^-51.5 T_j for r in [-2^-11, 2^-11] (half an ulp of T_j and the cubic's
-    error, about an ulp)."""
+    """Fixed point at 2^62, every entry positive (log2's coefficients as magnitudes of alternating
+    signs): log2 F_j and T_j are the nearest integers to their values * 2^62;
+    each entry's polynomial, with its coefficients as stored, is within its stated bound of the
+    function at 9 points of its interval (evaluated exactly in 120-bit arithmetic):
+    |log2 F_j + u q_j(u) - log2(F_j + u)| below 2^-58 for u in [0, 2^-10] (the cubic's error,
+    about 2^-58.5, and the coefficients' rounding), |T_j + r q_j(r) - T_j 2^r| below 2^-52.5 T_j
+    for r in [-2^-11, 2^-11] (the quadratic's error, at most 2^-52.7)."""
     t = parse(os.path.join(CSRC, "f64_math_tables.inc"))
     ln2 = mp.log(2)
-    for name in ("kLog2F", "kL2D1", "kL2D2", "kL2D3", "kL2D4", "kExp2J", "kExp2E1", "kExp2E2",
-                 "kExp2E3"):
+    one = mp.mpf(2) ** 62
+    for name in ("kFxLog2F", "kFxL2A1", "kFxL2A2", "kFxL2A3", "kFxL2A4", "kFxExp2T", "kFxExp2E1",
+                 "kFxExp2E2", "kFxExp2E3"):
         assert len(t[name]) == 1024, name
+        assert all(0 <= v < 2 ** 63 for v in t[name]), name
     h, he = mp.mpf(2) ** -10, mp.mpf(2) ** -11
     us = [h * i / 8 for i in range(9)]
     rs = [he * (i - 4) / 4 for i in range(9)]
     for j in range(1024):
         F = 1 + mp.mpf(j) / 1024
-        assert nearest_double(t["kLog2F"][j], mp.log(F) / ln2), j
-        d = [mp.mpf(t[f"kL2D{i}"][j]) for i in range(1, 5)]
+        assert abs(t["kFxLog2F"][j] - mp.log(F) / ln2 * one) <= 0.5, j
+        a = [mp.mpf(t[f"kFxL2A{i}"][j]) / one for i in range(1, 5)]
         for u in us:
-            p = mp.mpf(t["kLog2F"][j]) + u * (d[0] + u * (d[1] + u * (d[2] + u * d[3])))
-            assert abs(p - mp.log(F + u) / ln2) < mp.mpf(2) ** -53.5, (j, u)
+            p = mp.mpf(t["kFxLog2F"][j]) / one + u * (a[0] - u * (a[1] - u * (a[2] - u * a[3])))
+            assert abs(p - mp.log(F + u) / ln2) < mp.mpf(2) ** -58, (j, u)
         T = mp.power(2, mp.mpf(j) / 1024)
-        assert nearest_double(t["kExp2J"][j], T), j
-        e = [mp.mpf(t[f"kExp2E{i}"][j]) for i in range(1, 4)]
+        assert abs(t["kFxExp2T"][j] - T * one) <= 0.5, j
+        e = [mp.mpf(t[f"kFxExp2E{i}"][j]) / one for i in range(1, 4)]
         for r in rs:
-            p = mp.mpf(t["kExp2J"][j]) + r * (e[0] + r * (e[1] + r * e[2]))
-            assert abs(p - T * mp.power(2, r)) < T * mp.mpf(2) ** -51.5, (j, r)
+            p = mp.mpf(t["kFxExp2T"][j]) / one + r * (e[0] + r * (e[1] + r * e[2]))
+            assert abs(p - T * mp.power(2, r)) < T * mp.mpf(2) ** -52.5, (j, r)
     # The exact anchors the coincidence rule and powers of two rely on.
-    assert t["kLog2F"][0] == 0.0 and t["kExp2J"][0] == 1.0
-    assert t["kExp2J"][512] == float.fromhex("0x1.6a09e667f3bcdp+0")  # sqrt(2), rounded
+    assert t["kFxLog2F"][0] == 0 and t["kFxExp2T"][0] == 2 ** 62
 
 
 def test_double_float_tables_are_accurate_pairs(prec):
