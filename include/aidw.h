@@ -49,7 +49,10 @@ extern "C" {
 /* AIDW_F32C: distances, kNN selection and weights in FP32; the two weighted sums in FP32 with
  * Kahan-compensated merges; alpha mapping (Eq. 2, 4, 5, 6) and the final ratio in FP64.
  * Queries and the output are float arrays.
- * AIDW_F64: every step in FP64; queries and the output are double arrays.
+ * AIDW_F64: every step at double precision or finer: distances, kNN selection, alpha, the
+ * power scale, the weighted sum of z and the final ratio in FP64; log2, exp2 and the sum of the
+ * weights in 62-bit fixed point on the integer pipe (within about an ulp of the FP64 result).
+ * Queries and the output are double arrays.
  * AIDW_F64X (the library's addition; the paper has FP32 and FP64 only): FP64 arrays and the
  * FP64 path's phase 1, neighbour lists and alpha; in phase 2 each pair's squared distance is
  * formed in FP64 and the rest of its work (log2, the power of Eq. 1, both weighted sums) runs
