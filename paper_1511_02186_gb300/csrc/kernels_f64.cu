@@ -19,11 +19,14 @@ namespace {
 
 constexpr int kChunkKnn = 16;
 constexpr int kChunkW = 32;
-constexpr int kQW64 = 4;
+// FP64 phase-2 queries per thread (8,192 x 1M with 256-thread CTAs: 104.6 ms with 2, 109.0 ms
+// with 4, 161.8 ms with 8)
+constexpr int kQW64 = 2;
 constexpr int kTileW64 = 256;  // FP64 phase-2 tile (points), beside 72 KB of tables
-// FP64 phase-2 CTA: 8 warps share one copy of the tables (two CTAs per SM by shared memory, 16
-// warps: the integer steps of log2 / exp2 are long dependent chains that need the warps).
-constexpr int kThreadsW64 = 256;
+// FP64 phase-2 CTA: 16 warps share one copy of the tables, one CTA per SM by registers (72 a
+// thread): the integer steps of log2 / exp2 are long dependent chains that need the warps
+// (8,192 x 1M: 101.7 ms; two CTAs of 256 threads per SM 104.6 ms, one of 768 threads 109.6 ms).
+constexpr int kThreadsW64 = 512;
 
 __device__ __forceinline__ double dist2_exact(double qx, double qy, double px, double py)
 {
@@ -701,10 +704,9 @@ __device__ __forceinline__ void fixed_to_doubles(unsigned __int128 v, double &hi
     lo = __ll2double_rn(dA) * 0x1p-32 + __ull2double_rn(B) * 0x1p-96;
 }
 
-// Two CTAs of 256 threads per SM (12 KB of 256-point tiles plus 72 KB of tables each, 128
-// registers a thread).
+// One CTA of 512 threads per SM (12 KB of 256-point tiles plus 72 KB of tables).
 template <int Q>
-__global__ void __launch_bounds__(kThreadsW64, 2)
+__global__ void __launch_bounds__(kThreadsW64, 1)
 f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restrict__ qx,
                    const double *__restrict__ qy, const QParamF64 *__restrict__ qp,
                    double *__restrict__ part_sum, int *__restrict__ err)
@@ -769,7 +771,9 @@ f64_weights_kernel(DatasetDev ds, int64_t m, PassPlan pp, const double *__restri
 #pragma unroll
             for (int j = 0; j < Q; ++j)
                 sz[j] = 0.0;
-#pragma unroll 4
+            // One point at a time (the Q queries' chains interleave): 109.1 ms on 8,192 x 1M
+            // against 124.5 ms unrolled by 4 and 109.6 ms by 2.
+#pragma unroll 1
             for (int u = 0; u < kChunkW; ++u) {
                 const double2 p = txy[b][c + u];
                 const double pz = tz[b][c + u];
