@@ -112,3 +112,33 @@ def test_integer_reduction_edges():
     # k/1024 itself: exact up to the table entry's rounding (r = 0).
     lk, ek = probe(np.ones(16), np.arange(-8, 8) * step)
     assert np.all(np.abs(ek / np.exp2(np.arange(-8, 8) * step) - 1.0) <= ULP1)
+
+
+def test_kernels_match_the_integer_model_bit_for_bit():
+    """For every argument the library's log2 / exp2 give the doubles of the bit-exact model of
+    their integer steps (tests/f64_fixed_model.py), whose accuracy the CPU tests pin against
+    120-bit references: random arguments over the whole range, both ends of table intervals,
+    the rounding points of exp2's reduction, tiny and exactly representable arguments."""
+    import f64_fixed_model as fm
+    t = fm.load_tables()
+    rng = np.random.default_rng(6)
+    x = np.exp(rng.uniform(np.log(DBL_MIN), np.log(1e300), 12000))
+    j = rng.integers(0, 1024, 4000)
+    e = 2.0 ** rng.integers(-1022, 1000, 4000)
+    x = np.concatenate([x, (1.0 + j / 1024.0) * e,
+                        np.nextafter((1.0 + (j + 1) / 1024.0) * e, 0.0), [DBL_MIN, 1.0, np.inf]])
+    k = rng.integers(-1020 * 1024, 8 * 1024, 4000).astype(np.float64) / 1024.0
+    y = np.concatenate([rng.uniform(-1020.9, 8.0, 12000), k, k + 0.5 / 1024,
+                        np.nextafter(k + 0.5 / 1024, -np.inf),
+                        2.0 ** rng.uniform(-60, -11, 3000) * rng.choice([-1.0, 1.0], 3000),
+                        [0.0, -1.0, -1021.0, -1e300]])
+    y = y[y < 8.0]
+    n = max(len(x), len(y))
+    xs, ys = np.resize(x, n), np.resize(y, n)
+    lx, ey = probe(xs, ys)
+    ml = np.array([fm.log2_fx(float(a), t) for a in xs])
+    me = np.array([fm.exp2_fx(float(b), t)[0] for b in ys])
+    bad_l = np.flatnonzero(ml.view(np.int64) != lx.view(np.int64))
+    bad_e = np.flatnonzero(me.view(np.int64) != ey.view(np.int64))
+    assert bad_l.size == 0, [(xs[i], lx[i], ml[i]) for i in bad_l[:5]]
+    assert bad_e.size == 0, [(ys[i], ey[i], me[i]) for i in bad_e[:5]]
