@@ -7,7 +7,7 @@
 //     u q_j(u)), q_j a cubic per table entry (near-minimax: the polynomial interpolating
 //     log2(1 + u/F) / u at the Chebyshev nodes of [0, 2^-10]). The fraction log2 F + u q_j(u)
 //     is formed in 64-bit fixed point with 62 fraction bits, e added exactly at 52 fraction
-//     bits, and the sum rounded once to a double: absolute error within about half an ulp of
+//     bits, and the sum rounded once to a double: absolute error within 0.75 ulp of
 //     max(1, |log2 x|).
 //   exp2(y), y < 1023: y <= -1021 gives 0 (far below any weight that matters next to the nearest
 //     point's, which is 1); else k = round(1024 y), r = y - k/1024 in [-2^-11, 2^-11] (exact,

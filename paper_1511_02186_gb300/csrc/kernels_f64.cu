@@ -1,5 +1,6 @@
 // FP64 kernels of the AIDW hot path for sm_103a: the same two scans as the FP32 path with
-// every step in double precision (Sec. 3.2.1 builds its kernels for float and double alike).
+// every step at double precision or finer (Sec. 3.2.1 builds its kernels for float and double
+// alike; phase 2's log2, exp2 and sum of the weights run in 62-bit fixed point, f64_math.cuh).
 // Squared distances of phase 1 are formed as dx*dx + dy*dy with each product and sum rounded
 // separately, so neighbour lists agree bit for bit with a reference that evaluates the same
 // expression in IEEE double without fused multiply-add. Ties go to the lower index. Both
