@@ -578,17 +578,14 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
 {
     if (!ctx || max_batch_requests < 0 || streams < 0 || streams > 8 || max_queued < 0)
         return AIDW_ERR_INVALID_ARG;
+    const aidw_tune_config cfg = ctx_tune(ctx);
     {
+        // The check and the creation in one critical section: a submit on another thread
+        // creates the default runtime under the same lock.
         std::lock_guard<std::mutex> g(ctx_mutex(ctx));
         if (ctx_serving(ctx))
             return AIDW_ERR_INVALID_ARG;  // configure before the first submit
-    }
-    ServingRuntime *rt;
-    {
-        // Create stopped-free runtime with the requested shape.
-        const aidw_tune_config cfg = ctx_tune(ctx);
-        std::lock_guard<std::mutex> g(ctx_mutex(ctx));
-        rt = new ServingRuntime();
+        ServingRuntime *rt = new ServingRuntime();
         rt->ctx = ctx;
         rt->cfg = cfg;
         if (max_queued)
@@ -602,9 +599,9 @@ int aidw_serving_configure(aidw_ctx *ctx, size_t inflight_bytes, int32_t max_bat
             rt->n_slots = streams;
         cudaSetDevice(ctx_device(ctx));
         create_flights(rt);
+        rt->worker = std::thread(worker_main, rt);
         ctx_serving(ctx) = rt;
     }
-    rt->worker = std::thread(worker_main, rt);
     return AIDW_OK;
 }
 
